@@ -1,0 +1,216 @@
+/*
+ * truss.h -- C ABI of the GB300 truss decomposition library (libtruss.so).
+ *
+ * The library computes, for every undirected edge of a simple graph, its
+ * trussness: the largest k such that the edge belongs to a k-truss, a
+ * subgraph in which every edge lies in at least k-2 triangles of the
+ * subgraph (Kabir & Madduri, "Shared-memory Graph Truss Decomposition",
+ * §II).  Edges in no triangle have trussness 2.  The method is PKT (§III):
+ * per-edge triangle support (Algorithm 3), then level-synchronous peeling
+ * (Algorithm 4: Scan; Algorithm 5: ProcessSubLevel), run as CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *    owns every buffer it passes; the library owns the opaque truss_graph and
+ *    its device workspace, released by truss_free.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered: device work is enqueued on `stream`
+ *    and may still be running when the call returns, unless stated otherwise.
+ *  - Every call returns an int status (TRUSS_OK or a negative TRUSS_E*).
+ *    Nothing is thrown across the ABI; no kernel traps.  Errors found on
+ *    the device (a grid-barrier wait that exceeded its limit, an index out
+ *    of range) are latched in the graph handle and returned by the next call
+ *    that synchronises (truss_decompose with opts->sync = 1, truss_sync,
+ *    truss_num_edges after a build, and every host-buffer call).
+ *  - Canonical edge order: edge i is the i-th pair (min(u,v), max(u,v)) in
+ *    ascending lexicographic order of the INPUT vertex labels, after
+ *    self-loops and repeated pairs are dropped (§IV-A).  Every per-edge
+ *    output is in that order, whatever internal relabelling is used.
+ */
+#ifndef TRUSS_H
+#define TRUSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TRUSS_API __attribute__((visibility("default")))
+#else
+#define TRUSS_API
+#endif
+
+/* ------------------------------------------------------------- statuses */
+#define TRUSS_OK 0
+#define TRUSS_EINVAL (-1)    /* bad argument (null pointer, negative size)   */
+#define TRUSS_ENOMEM (-2)    /* device or host allocation failed             */
+#define TRUSS_ECUDA (-3)     /* a CUDA runtime call failed                   */
+#define TRUSS_ETIMEOUT (-4)  /* a device-side wait gave up (grid barrier)    */
+#define TRUSS_EOVERFLOW (-5) /* m or 2m does not fit the index width         */
+#define TRUSS_EBADGRAPH (-6) /* a vertex id outside [0, n)                   */
+#define TRUSS_EDEVICE (-7)   /* a device-side consistency check failed       */
+#define TRUSS_ENOTSUP (-8)   /* the requested form is not available here     */
+
+/* Human-readable text for a status.  Never NULL; static storage. */
+TRUSS_API const char* truss_strerror(int status);
+
+/* ---------------------------------------------------------------- graph */
+typedef struct truss_graph truss_graph;
+
+/* truss_build_csr flags */
+#define TRUSS_DEGREE_ORDER 1u /* relabel vertices by ascending degree inside
+                                 the library (results stay in input labels) */
+#define TRUSS_OFFSETS64 2u    /* store row offsets as int64 (else int32,
+                                 switched to int64 automatically when 2m
+                                 exceeds INT32_MAX)                          */
+
+/*
+ * truss_build_csr -- build the device graph of §III / Fig. 2 from a raw edge
+ * list: undirect, drop self-loops and repeated pairs (§IV-A), sort every
+ * adjacency row ascending (N, row offsets Es), give each slot its edge id
+ * (Eid), record the first slot whose neighbour exceeds the row vertex (Eo),
+ * and the endpoint pair of every edge (El).  With TRUSS_DEGREE_ORDER the
+ * vertices are relabelled by ascending degree first (the paper orders
+ * vertices by k-core number for the same purpose, §IV-B; trussness does not
+ * depend on the labelling).
+ *   d_src, d_dst : device int32[n_in], endpoint pairs; may hold self-loops,
+ *                  repeats and both orientations.  Read only; the caller may
+ *                  free them once the call has synchronised.
+ *   n_in         : number of pairs (>= 0).
+ *   n            : number of vertices; ids must lie in [0, n).
+ *   flags        : TRUSS_DEGREE_ORDER | TRUSS_OFFSETS64.
+ *   out          : receives the handle (NULL on failure).
+ * Synchronises `stream` before returning (the edge count sizes later
+ * buffers).  Returns TRUSS_EBADGRAPH for an id outside [0, n),
+ * TRUSS_EOVERFLOW if m >= 2^31-1, TRUSS_ENOMEM / TRUSS_ECUDA otherwise.
+ * m = 0 is valid.
+ */
+TRUSS_API int truss_build_csr(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t n, uint32_t flags,
+                    void* stream, truss_graph** out);
+
+/* Release the handle and all its device memory (NULL is ignored). */
+TRUSS_API void truss_free(truss_graph* g);
+
+/* Number of undirected edges m / vertices n of the built graph. */
+TRUSS_API int truss_num_edges(const truss_graph* g, int64_t* m);
+TRUSS_API int truss_num_vertices(const truss_graph* g, int32_t* n);
+
+/* Canonical edge list: d_u[i] < d_v[i], input labels, int32[m] each. */
+TRUSS_API int truss_edge_list(const truss_graph* g, int32_t* d_u, int32_t* d_v, void* stream);
+
+/*
+ * truss_csr_copy -- copy the internal augmented CSR (Fig. 2) for inspection:
+ * d_rowptr int64[n+1] (Es), d_col int32[2m] (N), d_eid int32[2m] (Eid, in
+ * canonical edge ids), d_eo int64[n] (Eo).  Internal vertex labels: with
+ * TRUSS_DEGREE_ORDER they differ from the input labels, and d_order (int32[n],
+ * may be NULL) receives the input label of each internal vertex.
+ */
+TRUSS_API int truss_csr_copy(const truss_graph* g, int64_t* d_rowptr, int32_t* d_col, int32_t* d_eid, int64_t* d_eo,
+                   int32_t* d_order, void* stream);
+
+/*
+ * truss_support -- per-edge triangle count S(e), the number of triangles
+ * containing e (§II), computed by the oriented vertex-iterator of
+ * Algorithm 3 (each triangle u < v < w found once, +1 on its three edges).
+ *   d_support : device int32[m], canonical order (written).
+ */
+TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
+
+/* ------------------------------------------------------- decomposition */
+
+/* level-loop forms (how the sub-levels of Algorithm 4 are driven) */
+#define TRUSS_LOOP_PLAIN 0      /* host loop, one launch per phase; the host
+                                   reads the frontier size every sub-level */
+#define TRUSS_LOOP_PERSISTENT 1 /* one cooperative kernel, grid barriers with
+                                   a time limit between phases            */
+
+/* ProcessSubLevel kernel variants (all exact) */
+#define TRUSS_VAR_AUTO (-1)   /* per-edge choice by the built-in heuristic   */
+#define TRUSS_VAR_THREAD 0    /* one thread per frontier edge               */
+#define TRUSS_VAR_WARP 1      /* one warp per frontier edge                 */
+#define TRUSS_VAR_BLOCK 2     /* one thread block per frontier edge         */
+
+typedef struct truss_opts {
+    int32_t loop;        /* TRUSS_LOOP_*                                      */
+    int32_t variant;     /* TRUSS_VAR_*                                       */
+    int32_t sync;        /* nonzero: synchronise before returning and report
+                            device-side errors                                */
+    int32_t level_jump;  /* nonzero: after an empty Scan, continue at the
+                            smallest live support instead of l+1 (same result,
+                            fewer empty scans)                                */
+    int64_t timeout_ns;  /* limit on each device-side wait (0: 10 s)          */
+    int32_t* h_sub_level; /* optional host arrays: level l and frontier size */
+    int64_t* h_sub_size;  /* |curr| of every non-empty sub-level, in order   */
+    int64_t max_sub;      /* their capacity (entries); needs sync = 1        */
+    int32_t reserved[8];
+} truss_opts;
+
+typedef struct truss_stats {
+    int64_t m;           /* undirected edges                                 */
+    int64_t sublevels;   /* non-empty sub-levels (frontiers) processed       */
+    int64_t scans;       /* Scan passes over the support array               */
+    int64_t triangles;   /* number of triangles (sum of support / 3)         */
+    int32_t t_max;       /* largest trussness (0 when m = 0)                 */
+    int32_t levels;      /* levels with at least one edge                    */
+    float ms_support;    /* device time of the support phase (sync = 1)      */
+    float ms_peel;       /* device time of the peeling phase (sync = 1)      */
+    int64_t reserved[6];
+} truss_stats;
+
+/* Fill *opts with defaults: persistent loop, heuristic variants, no sync,
+ * level jumps on, 10 s wait limit, no sub-level recording. */
+TRUSS_API void truss_default_opts(truss_opts* opts);
+
+/*
+ * truss_decompose -- trussness of every edge (§II) by PKT: support
+ * (Algorithm 3), then, level l = 0, 1, ...: Scan gathers the edges whose
+ * support equals l (Algorithm 4); ProcessSubLevel (Algorithm 5) walks the
+ * triangles of each such edge whose other two edges are unprocessed and
+ * lowers the support of those other edges that are above l, by one per
+ * triangle, never below l; edges that reach l form the next sub-level.  When
+ * two edges of a triangle are in the same sub-level, the lower edge id
+ * handles it (§III, Fig. 3).  Trussness = final support + 2.
+ *   d_truss : device int32[m], canonical order (written).
+ *   opts    : NULL for defaults (truss_default_opts).
+ *   stats   : may be NULL; filled only when opts->sync is set.
+ */
+TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts* opts, truss_stats* stats, void* stream);
+
+/*
+ * truss_peel_sublevel -- one ProcessSubLevel (Algorithm 5) on a caller-set
+ * state, for tests and tuning.  All arrays are device arrays in canonical
+ * edge order:
+ *   d_S     : int32[m] support, updated in place;
+ *   d_flags : uint8[m], bit 0 = processed, bit 1 = in curr; on return curr
+ *             edges are processed and not in curr, next edges are in curr;
+ *   d_curr  : int32[ncurr] canonical edge ids, all with d_S == l (their
+ *             in-curr bit is set by the call);
+ *   d_next  : int32[m] receives the next frontier (any order);
+ *   h_nnext : host int64, receives |next|.
+ * Synchronises `stream`.
+ */
+TRUSS_API int truss_peel_sublevel(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr, int64_t ncurr,
+                        int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant, void* stream);
+
+/*
+ * truss_decompose_host -- the whole pipeline from host memory: copy the raw
+ * edge list h_src/h_dst (int32[n_in], host; pinned memory is fastest) to the
+ * device, build the graph (flags as truss_build_csr), decompose, and copy
+ * the trussness back to h_truss (host int32, capacity m_cap >= m, canonical
+ * order).  *m_out receives m.  Synchronous.  Device workspace is allocated
+ * and freed inside the call.
+ */
+TRUSS_API int truss_decompose_host(const int32_t* h_src, const int32_t* h_dst, int64_t n_in, int32_t n, uint32_t flags,
+                         int32_t* h_truss, int64_t m_cap, int64_t* m_out, const truss_opts* opts,
+                         truss_stats* stats, void* stream);
+
+/* Wait for the graph's pending device work on `stream` and return any
+ * latched device-side error (and clear it). */
+TRUSS_API int truss_sync(truss_graph* g, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRUSS_H */

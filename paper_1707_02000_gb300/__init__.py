@@ -1,0 +1,255 @@
+"""Python binding of libtruss.so: GB300 truss decomposition (PKT).
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/truss.h``; PyTorch provides
+device memory and streams.  There is no CPU fallback: importing this module
+without a built ``libtruss.so`` raises, and every call needs a CUDA device.
+
+Typical use::
+
+    import torch, paper_1707_02000_gb300 as pkt
+    g = pkt.build_csr(src_cuda_int32, dst_cuda_int32, n)
+    tau = g.decompose()            # int32[m] on the GPU, canonical edge order
+    u, v = g.edge_list()           # the canonical edges, input labels
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtruss.so")
+
+OK = 0
+EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP = -1, -2, -3, -4, -5, -6, -7, -8
+DEGREE_ORDER = 1
+OFFSETS64 = 2
+LOOP_PLAIN, LOOP_PERSISTENT = 0, 1
+VAR_AUTO, VAR_THREAD, VAR_WARP, VAR_BLOCK = -1, 0, 1, 2
+PROCESSED, IN_CURR = 1, 2
+
+# Every symbol include/truss.h declares (checked by the tests).
+EXPORTS = (
+    "truss_strerror", "truss_build_csr", "truss_free", "truss_num_edges", "truss_num_vertices",
+    "truss_edge_list", "truss_csr_copy", "truss_support", "truss_default_opts", "truss_decompose",
+    "truss_peel_sublevel", "truss_decompose_host", "truss_sync",
+)
+
+
+class TrussError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("loop", ctypes.c_int32), ("variant", ctypes.c_int32), ("sync", ctypes.c_int32),
+                ("level_jump", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
+                ("h_sub_level", ctypes.POINTER(ctypes.c_int32)), ("h_sub_size", ctypes.POINTER(ctypes.c_int64)),
+                ("max_sub", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("sublevels", ctypes.c_int64), ("scans", ctypes.c_int64),
+                ("triangles", ctypes.c_int64), ("t_max", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+def _declare(lib):
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    lib.truss_strerror.argtypes = [ctypes.c_int]
+    lib.truss_strerror.restype = ctypes.c_char_p
+    lib.truss_build_csr.argtypes = [vp, vp, i64, i32, u32, vp, pp]
+    lib.truss_free.argtypes = [vp]
+    lib.truss_free.restype = None
+    lib.truss_num_edges.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.truss_num_vertices.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.truss_edge_list.argtypes = [vp, vp, vp, vp]
+    lib.truss_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.truss_support.argtypes = [vp, vp, vp]
+    lib.truss_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.truss_default_opts.restype = None
+    lib.truss_decompose.argtypes = [vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
+    lib.truss_peel_sublevel.argtypes = [vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(i64), i32, vp]
+    lib.truss_decompose_host.argtypes = [vp, vp, i64, i32, u32, vp, i64, ctypes.POINTER(i64),
+                                         ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
+    lib.truss_sync.argtypes = [vp, vp]
+    for name in EXPORTS:
+        if name not in ("truss_strerror", "truss_free", "truss_default_opts"):
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+                      " (there is no CPU fallback)")
+_lib = _declare(ctypes.CDLL(LIB_PATH))
+
+
+def library():
+    """The loaded ctypes library (for tests of the raw C ABI)."""
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return _lib.truss_strerror(status).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise TrussError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    assert t.is_cuda and t.is_contiguous(), "expects a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.truss_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A device-resident graph handle (owns its device memory)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        m = ctypes.c_int64()
+        n = ctypes.c_int32()
+        _check(_lib.truss_num_edges(self._h, ctypes.byref(m)), "truss_num_edges")
+        _check(_lib.truss_num_vertices(self._h, ctypes.byref(n)), "truss_num_vertices")
+        self.m = int(m.value)
+        self.n = int(n.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.truss_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _empty(self, k):
+        torch = _torch()
+        return torch.empty(max(k, 1), dtype=torch.int32, device="cuda")[:k]
+
+    def edge_list(self, stream=None):
+        u, v = self._empty(self.m), self._empty(self.m)
+        _check(_lib.truss_edge_list(self._h, _dptr(u) if self.m else None, _dptr(v) if self.m else None,
+                                    _stream(stream)), "truss_edge_list")
+        return u, v
+
+    def csr(self, stream=None):
+        torch = _torch()
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        eo = torch.empty(max(self.n, 1), dtype=torch.int64, device="cuda")
+        col, eid = self._empty(2 * self.m), self._empty(2 * self.m)
+        order = self._empty(self.n)
+        _check(_lib.truss_csr_copy(self._h, _dptr(rp), _dptr(col) if self.m else None,
+                                   _dptr(eid) if self.m else None, _dptr(eo), _dptr(order) if self.n else None,
+                                   _stream(stream)), "truss_csr_copy")
+        return rp, col, eid, eo[: self.n], order
+
+    def support(self, out=None, stream=None):
+        out = self._empty(self.m) if out is None else out
+        _check(_lib.truss_support(self._h, _dptr(out) if self.m else None, _stream(stream)), "truss_support")
+        return out
+
+    def decompose(self, out=None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, sync=True, level_jump=True,
+                  timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False):
+        """Trussness (int32[m], canonical order).  With ``record`` also
+        returns the (level, |curr|) of every sub-level; with ``stats`` a
+        dict of run statistics."""
+        out = self._empty(self.m) if out is None else out
+        o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record)),
+                         level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
+        rl = rs = None
+        if record:
+            rl = np.zeros(max_sub, np.int32)
+            rs = np.zeros(max_sub, np.int64)
+            o.h_sub_level = rl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            o.h_sub_size = rs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            o.max_sub = max_sub
+        st = Stats()
+        _check(_lib.truss_decompose(self._h, _dptr(out) if self.m else None, ctypes.byref(o),
+                                    ctypes.byref(st), _stream(stream)), "truss_decompose")
+        res = [out]
+        if record:
+            k = min(int(st.sublevels), max_sub)
+            res.append((rl[:k].copy(), rs[:k].copy()))
+        if stats:
+            res.append(st.as_dict())
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def peel_sublevel(self, S, flags, curr, l, variant=VAR_AUTO, stream=None):
+        """One ProcessSubLevel on a caller-set state (device tensors, canonical
+        order); S and flags are updated in place.  Returns next (device)."""
+        nxt = self._empty(self.m)
+        k = ctypes.c_int64()
+        _check(_lib.truss_peel_sublevel(self._h, _dptr(S) if self.m else None, _dptr(flags) if self.m else None,
+                                        _dptr(curr) if curr.numel() else None, curr.numel(), l,
+                                        _dptr(nxt) if self.m else None, ctypes.byref(k), variant,
+                                        _stream(stream)), "truss_peel_sublevel")
+        return nxt[: k.value]
+
+    def sync(self, stream=None):
+        _check(_lib.truss_sync(self._h, _stream(stream)), "truss_sync")
+
+
+def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = False, stream=None) -> Graph:
+    """Device graph from CUDA int32 tensors ``src``, ``dst`` (raw pairs)."""
+    assert src.dtype == dst.dtype and str(src.dtype) == "torch.int32" and src.numel() == dst.numel()
+    flags = (DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
+    h = ctypes.c_void_p()
+    k = src.numel()
+    _check(_lib.truss_build_csr(_dptr(src) if k else None, _dptr(dst) if k else None, k, n, flags,
+                                _stream(stream), ctypes.byref(h)), "truss_build_csr")
+    return Graph(h)
+
+
+def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool = True, offsets64: bool = False,
+                   out: np.ndarray | None = None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None):
+    """Host arrays in, host trussness out (canonical order): the C ABI's
+    truss_decompose_host.  ``src``/``dst`` should be pinned for speed."""
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    cap = src.shape[0] if out is None else out.shape[0]
+    out = np.empty(max(cap, 1), np.int32) if out is None else out
+    flags = (DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
+    m = ctypes.c_int64()
+    o = default_opts(loop=loop, variant=variant, sync=1)
+    st = Stats()
+    _check(_lib.truss_decompose_host(src.ctypes.data_as(ctypes.c_void_p), dst.ctypes.data_as(ctypes.c_void_p),
+                                     src.shape[0], n, flags, out.ctypes.data_as(ctypes.c_void_p), cap,
+                                     ctypes.byref(m), ctypes.byref(o), ctypes.byref(st), _stream(stream)),
+           "truss_decompose_host")
+    return out[: m.value], st.as_dict()

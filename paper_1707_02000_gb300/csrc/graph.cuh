@@ -1,0 +1,66 @@
+// Device-resident graph handle shared by the build, support and peel units.
+//
+// HBM layout (internal vertex labels; with TRUSS_DEGREE_ORDER a vertex's
+// label is its rank by (degree, input label)):
+//   rowptr Off[n+1]   Es of Fig. 2: row offsets of the symmetric adjacency
+//   eo     Off[n]     Eo of Fig. 2: first slot of row u whose neighbour > u
+//   col    int32[2m]  N of Fig. 2: neighbours, every row ascending
+//   eid    int32[2m]  Eid of Fig. 2: internal edge id of every slot
+//   el     int2[m]    El of Fig. 2: endpoints (x < y) of internal edge e;
+//                     internal ids are the lexicographic order of (x, y)
+//   perm   int32[m]   internal edge id -> canonical (input-label) edge id;
+//                     NULL when no relabelling is done (identity)
+//   order  int32[n]   internal vertex -> input label; NULL = identity
+// Peeling state (allocated on first decomposition):
+//   ss     int2[m]    {S, stamp} per internal edge.  S is the live support;
+//                     stamp is the number of the sub-level whose frontier
+//                     the edge entered (INT32_MAX while it has entered none).
+//                     During sub-level g: processed <=> stamp < g, in curr
+//                     <=> stamp == g (the processed / inCurr / inNext arrays
+//                     of Algorithms 4-5 folded into one word, so finishing a
+//                     sub-level needs no pass over curr: g+1 flips them all).
+//   fr[2]  int32[m]   curr / next frontiers (ping-pong)
+//   ctr    int[...]   device counters (see peel.cu)
+#pragma once
+#include "common.cuh"
+
+#define TRUSS_STAMP_NONE 0x7fffffff
+
+// Support-kernel split: vertices whose upper degree d+(u) exceeds this are
+// handled by the block-per-vertex kernel instead of warp-per-vertex.
+#define TRUSS_SUP_WARP_CAP 256
+#define TRUSS_SUP_BLOCK_CAP 12288
+
+struct truss_graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    int off64 = 0;
+    int device = 0;
+    int sms = 0;
+    void* rowptr = nullptr;
+    void* eo = nullptr;
+    int32_t* col = nullptr;
+    int32_t* eid = nullptr;
+    int2* el = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* order = nullptr;
+    // vertices by upper degree for the support kernels
+    int32_t* sup_big = nullptr;   // d+ in (WARP_CAP, BLOCK_CAP]
+    int32_t n_sup_big = 0;
+    int32_t* sup_huge = nullptr;  // d+ > BLOCK_CAP
+    int32_t n_sup_huge = 0;
+    int64_t max_deg = 0;
+    int64_t max_updeg = 0;
+    // peeling workspace
+    int2* ss = nullptr;
+    int32_t* fr[2] = {nullptr, nullptr};
+    int* ctr = nullptr;
+    int* h_ctr = nullptr;  // pinned host mirror
+    int latched = 0;       // latched device-side error status
+};
+
+// Implemented in support.cu: fills ss[e].x = S(e) for every internal edge.
+int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s);
+// Implemented in peel.cu.
+int truss_ensure_workspace(truss_graph* g);
+void truss_release_workspace(truss_graph* g);

@@ -1,0 +1,267 @@
+// K1: per-edge triangle support (Algorithm 3, §III "Parallel support
+// computation").
+//
+// Vertices carry the library's internal order (ascending degree when the
+// graph was built with TRUSS_DEGREE_ORDER), and N+(u) is the part of row u
+// above u (slots [Eo[u], Es[u+1])).  Each triangle u < v < w is found exactly
+// once, at its lowest vertex u: for every v in N+(u) and every w in N+(v),
+// w closes a triangle iff w is in N+(u).  This is Algorithm 3's mark-and-
+// probe with X held in shared memory (the paper visits the middle vertex;
+// visiting the lowest one finds the same set of triangles, each once).
+//
+// GB300 mapping:
+//  - warp per vertex (d+(u) <= TRUSS_SUP_WARP_CAP): N+(u) is staged in shared
+//    memory with a counter per entry and the prefix of d+(v) over v in N+(u);
+//    the 32 lanes then walk the concatenation of all N+(v) lists as one flat
+//    range (balanced within the warp, coalesced reads of each N+(v)), and
+//    probe each w by binary search in the staged N+(u);
+//  - block per vertex for larger d+(u) (listed at build time), same scheme
+//    with the block's shared memory;
+//  - global-memory fallback for d+(u) beyond the shared-memory capacity.
+// Supports of the edges {u, x}, x in N+(u), are accumulated in shared
+// counters and added once per edge; only the {v, w} edges take one global
+// atomic per triangle.
+#include <algorithm>
+
+#include "graph.cuh"
+
+namespace {
+
+constexpr int SW_WARPS = 8;  // warps per block, warp-per-vertex kernel
+constexpr int SW_CAP = TRUSS_SUP_WARP_CAP;
+
+// S(e) lives in ss[e].x; the int view puts it at index 2e.
+__device__ __forceinline__ void add_support(int* S2, int32_t e, int v) { atomicAdd(S2 + 2 * (int64_t)e, v); }
+
+// Largest index p in [0, d) with P[p] <= idx (P ascending, P[0] = 0).
+__device__ __forceinline__ int seg_of(const int* P, int d, int idx) {
+    int lo = 0, hi = d - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P[mid] <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// First position in [lo, hi) with K[pos] >= w (K ascending); hi if none.
+__device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, int w) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (K[mid] < w) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(SW_WARPS * 32)
+    k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
+                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S2) {
+    __shared__ int sK[SW_WARPS][SW_CAP];
+    __shared__ int sC[SW_WARPS][SW_CAP];
+    __shared__ int sP[SW_WARPS][SW_CAP + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* K = sK[warp];
+    int* C = sC[warp];
+    int* P = sP[warp];
+    const int64_t nwarps = (int64_t)gridDim.x * SW_WARPS;
+    for (int64_t u = blockIdx.x * (int64_t)SW_WARPS + warp; u < n; u += nwarps) {
+        const Off up0 = eo[u], up1 = rowptr[u + 1];
+        const int d = (int)(up1 - up0);
+        if (d < 2 || d > SW_CAP) continue;  // no triangle at u / handled by the block kernels
+        // stage N+(u), zero counters, prefix of d+(v)
+        int carry = 0;
+        for (int b = 0; b < d; b += 32) {
+            int p = b + lane;
+            int dv = 0;
+            if (p < d) {
+                int v = __ldg(col + up0 + p);
+                K[p] = v;
+                C[p] = 0;
+                dv = (int)(__ldg(rowptr + v + 1) - __ldg(eo + v));
+            }
+            int x = dv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL_MASK, x, o);
+                if (lane >= o) x += y;
+            }
+            if (p < d) P[p] = carry + x - dv;
+            carry += __shfl_sync(FULL_MASK, x, 31);
+        }
+        if (lane == 0) P[d] = carry;
+        __syncwarp();
+        const int total = carry;
+        for (int idx = lane; idx < total; idx += 32) {
+            int p = seg_of(P, d, idx);
+            int v = K[p];
+            Off q = __ldg(eo + v) + (idx - P[p]);
+            int w = __ldg(col + q);
+            int r = lower_bound_smem(K, p + 1, d, w);
+            if (r < d && K[r] == w) {
+                atomicAdd(&C[r], 1);  // edge {u, w}
+                atomicAdd(&C[p], 1);  // edge {u, v}
+                add_support(S2, __ldg(eid + q), 1);  // edge {v, w}
+            }
+        }
+        __syncwarp();
+        for (int p = lane; p < d; p += 32)
+            if (C[p]) add_support(S2, __ldg(eid + up0 + p), C[p]);
+        __syncwarp();
+    }
+}
+
+constexpr int SB_THREADS = 512;
+
+// Block-wide inclusive scan helper for the prefix of d+(v).
+__device__ int block_scan_incl(int x, int* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < SB_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL_MASK, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SB_THREADS / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    int r = x + (warp ? wsum[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// One block per listed vertex; cap entries of K, C, P in dynamic shared memory.
+template <typename Off>
+__global__ void __launch_bounds__(SB_THREADS)
+    k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
+                    const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
+                    int* __restrict__ S2) {
+    extern __shared__ int smem[];
+    int* K = smem;
+    int* C = smem + cap;
+    int* P = smem + 2 * cap;  // cap + 1 entries
+    __shared__ int wsum[SB_THREADS / 32];
+    __shared__ int s_carry;
+    for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
+        const int32_t u = verts[i];
+        const Off up0 = eo[u], up1 = rowptr[u + 1];
+        const int d = (int)(up1 - up0);
+        if (threadIdx.x == 0) s_carry = 0;
+        __syncthreads();
+        for (int b = 0; b < d; b += SB_THREADS) {
+            int p = b + threadIdx.x;
+            int dv = 0;
+            if (p < d) {
+                int v = __ldg(col + up0 + p);
+                K[p] = v;
+                C[p] = 0;
+                dv = (int)(__ldg(rowptr + v + 1) - __ldg(eo + v));
+            }
+            int incl = block_scan_incl(dv, wsum);
+            int carry = s_carry;
+            if (p < d) P[p] = carry + incl - dv;
+            __syncthreads();
+            if (threadIdx.x == SB_THREADS - 1) s_carry = carry + incl;
+            __syncthreads();
+        }
+        const int total = s_carry;
+        if (threadIdx.x == 0) P[d] = total;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < total; idx += SB_THREADS) {
+            int p = seg_of(P, d, idx);
+            int v = K[p];
+            Off q = __ldg(eo + v) + (idx - P[p]);
+            int w = __ldg(col + q);
+            int r = lower_bound_smem(K, p + 1, d, w);
+            if (r < d && K[r] == w) {
+                atomicAdd(&C[r], 1);
+                atomicAdd(&C[p], 1);
+                add_support(S2, __ldg(eid + q), 1);
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < d; p += SB_THREADS)
+            if (C[p]) add_support(S2, __ldg(eid + up0 + p), C[p]);
+        __syncthreads();
+    }
+}
+
+// Vertices whose N+(u) exceeds shared memory: one block per vertex, one warp
+// per v in N+(u), probes by binary search in the global row of u.
+template <typename Off>
+__global__ void __launch_bounds__(SB_THREADS)
+    k_support_global(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
+                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts,
+                     int* __restrict__ S2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
+        const int32_t u = verts[i];
+        const Off up0 = eo[u], up1 = rowptr[u + 1];
+        for (Off pv = up0 + warp; pv < up1; pv += SB_THREADS / 32) {
+            const int v = __ldg(col + pv);
+            const Off v0 = __ldg(eo + v), v1 = __ldg(rowptr + v + 1);
+            int cuv = 0;
+            for (Off q = v0 + lane; q < v1; q += 32) {
+                int w = __ldg(col + q);
+                Off r = find_dev<Off>(col, pv + 1, up1, w);
+                if (r >= 0) {
+                    cuv++;
+                    add_support(S2, __ldg(eid + r), 1);
+                    add_support(S2, __ldg(eid + q), 1);
+                }
+            }
+            cuv = warp_sum(cuv);
+            if (lane == 0 && cuv) add_support(S2, __ldg(eid + pv), cuv);
+        }
+    }
+}
+
+__global__ void k_init_ss(int2* __restrict__ ss, int64_t m) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        ss[e] = make_int2(0, TRUSS_STAMP_NONE);
+}
+
+template <typename Off>
+int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
+    const Off* rowptr = (const Off*)g->rowptr;
+    const Off* eo = (const Off*)g->eo;
+    int* S2 = (int*)ss;
+    k_init_ss<<<grid_for(g->m, 256), 256, 0, s>>>(ss, g->m);
+    CU(cudaGetLastError());
+    if (g->n > 0 && g->m > 0) {
+        int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
+        k_support_warp<Off><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
+        CU(cudaGetLastError());
+    }
+    if (g->n_sup_big > 0) {
+        const int cap = TRUSS_SUP_BLOCK_CAP;
+        const size_t smem = sizeof(int) * (size_t)(3 * cap + 1);
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(Off) == 8]) {
+            CU(cudaFuncSetAttribute(k_support_block<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set[sizeof(Off) == 8] = true;
+        }
+        int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
+        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S2);
+        CU(cudaGetLastError());
+    }
+    if (g->n_sup_huge > 0) {
+        int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
+        k_support_global<Off><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S2);
+        CU(cudaGetLastError());
+    }
+    return TRUSS_OK;
+}
+
+}  // namespace
+
+int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s) {
+    return g->off64 ? support_impl<int64_t>(g, ss, s) : support_impl<int32_t>(g, ss, s);
+}

@@ -1,0 +1,318 @@
+"""CUDA path vs the CPU oracle, element by element (bit-exact: every output is
+an integer).  All calls go through the C ABI (libtruss.so) via the binding."""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pkt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1707_02000_gb300 as pkt
+
+    return pkt
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def small_graphs():
+    out = [("rmat10", gg.workload("rmat10_ef8")),
+           ("rmat8_s7", gg.rmat(8, 16, seed=7)),
+           ("chunglu", gg.chung_lu(4000, 2.1, 16.0, 400.0, seed=11)),
+           ("rgg", gg.rgg2d(4000, 24.0, seed=12))]
+    for s in range(4):
+        out.append((f"gnp{s}", gg.small_random(40 + 10 * s, 0.35, seed=300 + s)))
+    return out
+
+
+SMALL = small_graphs()
+
+
+def _flags(relabel, off64):
+    return dict(degree_order=relabel, offsets64=off64)
+
+
+# ------------------------------------------------------------------ build
+
+def test_fig2_csr_layout(pkt):
+    """Fig. 2: the augmented CSR of the n = 4, m = 5 graph, built without
+    relabelling, matches the layout derived by hand in the fixture."""
+    lines = open(os.path.join(GOLD, "fig2_diamond.txt")).read().splitlines()
+    want = {}
+    for ln in lines:
+        for key in ("Es", "N", "Eid"):
+            if ln.startswith(f"#   {key} ") and "=" in ln:
+                want[key] = [int(x) for x in ln.split("=")[1].replace("|", " ").split()]
+        if ln.startswith("#   Eo"):
+            want["Eo"] = [int(x) for x in ln.split("=")[1].split()]
+    rows = [ln.split() for ln in lines if ln and not ln.startswith("#")]
+    src = np.array([int(r[0]) for r in rows], np.int32)
+    dst = np.array([int(r[1]) for r in rows], np.int32)
+    G = pkt.build_csr(dev(src), dev(dst), 4, degree_order=False)
+    rp, col, eid, eo, order = G.csr()
+    assert host(rp).tolist() == want["Es"]
+    assert host(col).tolist() == want["N"]
+    assert host(eid).tolist() == want["Eid"]
+    assert host(eo).tolist() == want["Eo"]
+    assert host(order).tolist() == [0, 1, 2, 3]
+    assert host(G.support()).tolist() == [int(r[2]) for r in rows]
+    assert host(G.decompose()).tolist() == [int(r[3]) for r in rows]
+
+
+@pytest.mark.parametrize("relabel,off64", [(True, False), (False, False), (True, True)])
+@pytest.mark.parametrize("name,g", SMALL)
+def test_edge_list_and_support(pkt, name, g, relabel, off64):
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, **_flags(relabel, off64))
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    u, v = G.edge_list()
+    assert G.m == eu.size
+    assert np.array_equal(host(u), eu) and np.array_equal(host(v), ev)
+    assert np.array_equal(host(G.support()), oracle.support(g.n, eu, ev))
+    # the internal CSR is a valid sorted adjacency with consistent edge ids
+    rp, col, eid, eo, order = (host(x) for x in G.csr())
+    assert rp[0] == 0 and rp[-1] == 2 * eu.size
+    lab = order  # internal vertex -> input label
+    for x in range(0, g.n, max(1, g.n // 50)):
+        row = col[rp[x]:rp[x + 1]]
+        assert np.all(np.diff(row) > 0)
+        assert eo[x] == rp[x] + np.searchsorted(row, x + 1)
+        ids = eid[rp[x]:rp[x + 1]]
+        a, b = lab[x], lab[row]
+        assert np.array_equal(eu[ids], np.minimum(a, b)) and np.array_equal(ev[ids], np.maximum(a, b))
+
+
+# ------------------------------------------------------------ decomposition
+
+LOOPS = ["plain", "persistent"]
+VARIANTS = ["auto", "thread", "warp", "block"]
+
+
+def _loop(pkt, name):
+    return {"plain": pkt.LOOP_PLAIN, "persistent": pkt.LOOP_PERSISTENT}[name]
+
+
+def _var(pkt, name):
+    return {"auto": pkt.VAR_AUTO, "thread": pkt.VAR_THREAD, "warp": pkt.VAR_WARP, "block": pkt.VAR_BLOCK}[name]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("loop", LOOPS)
+@pytest.mark.parametrize("name,g", SMALL)
+def test_decompose_matches_oracle(pkt, name, g, loop, variant):
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    tau = G.decompose(loop=_loop(pkt, loop), variant=_var(pkt, variant))
+    eu, ev, want = oracle.truss_of_edges(g.n, g.src, g.dst)
+    assert np.array_equal(host(tau), want)
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+@pytest.mark.parametrize("relabel,off64", [(True, False), (False, False), (False, True)])
+def test_sublevel_frontiers_match_serial_run(pkt, loop, relabel, off64):
+    """The frontier of every sub-level is a function of the state, so the
+    device must produce exactly the serial run's (level, |curr|) sequence."""
+    for name, g in SMALL[:4]:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, **_flags(relabel, off64))
+        tau, (lv, sz) = G.decompose(loop=_loop(pkt, loop), record=True, level_jump=True)
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        want, olv, osz = oracle.pkt_serial(g.n, eu, ev)
+        assert np.array_equal(host(tau), want), name
+        assert np.array_equal(lv, olv) and np.array_equal(sz, osz), name
+
+
+def test_level_jump_off_gives_same_result(pkt):
+    g = gg.rgg2d(3000, 24.0, seed=5)
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    a = host(G.decompose(level_jump=False, loop=pkt.LOOP_PLAIN))
+    b = host(G.decompose(level_jump=True, loop=pkt.LOOP_PERSISTENT))
+    c = host(G.decompose(level_jump=False, loop=pkt.LOOP_PERSISTENT))
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert np.array_equal(a, oracle.truss_of_edges(g.n, g.src, g.dst)[2])
+
+
+def test_all_graphs_on_five_vertices(pkt):
+    """Every labelled graph on 5 vertices through the device path."""
+    import itertools
+
+    pairs = list(itertools.combinations(range(5), 2))
+    for mask in range(1 << 10):
+        sel = [pairs[i] for i in range(10) if mask >> i & 1]
+        if not sel:
+            continue
+        src = np.array([a for a, _ in sel], np.int32)
+        dst = np.array([b for _, b in sel], np.int32)
+        G = pkt.build_csr(dev(src), dev(dst), 5)
+        tau = host(G.decompose(loop=pkt.LOOP_PERSISTENT if mask & 1 else pkt.LOOP_PLAIN))
+        assert np.array_equal(tau, oracle.truss_of_edges(5, src, dst)[2]), sel
+        G.free()
+
+
+def test_random_small_graphs(pkt):
+    rng = np.random.default_rng(17)
+    for t in range(60):
+        n = int(rng.integers(3, 15))
+        g = gg.small_random(n, float(rng.uniform(0.2, 0.9)), seed=900 + t)
+        if g.n_in == 0:
+            continue
+        G = pkt.build_csr(dev(g.src), dev(g.dst), n, degree_order=bool(t & 1))
+        tau = host(G.decompose(variant=int(rng.integers(-1, 3))))
+        assert np.array_equal(tau, oracle.truss_of_edges(n, g.src, g.dst)[2])
+
+
+def test_closed_forms(pkt):
+    import itertools
+
+    for n in (3, 8, 33, 70):  # K_n: every edge has trussness n
+        pr = np.array(list(itertools.combinations(range(n), 2)), np.int32)
+        G = pkt.build_csr(dev(pr[:, 0]), dev(pr[:, 1]), n)
+        assert np.all(host(G.decompose()) == n)
+        assert np.all(host(G.support()) == n - 2)
+    # a long path and a big star: no triangles
+    n = 5000
+    G = pkt.build_csr(dev(np.arange(n - 1)), dev(np.arange(1, n)), n)
+    assert np.all(host(G.decompose()) == 2)
+    G = pkt.build_csr(dev(np.zeros(n - 1)), dev(np.arange(1, n)), n)
+    assert np.all(host(G.decompose()) == 2)
+    # wheel with a 3000-vertex rim: hub row long enough for the block path
+    k = 3000
+    src = np.concatenate([np.zeros(k), np.arange(1, k + 1)])
+    dst = np.concatenate([np.arange(1, k + 1), np.arange(1, k + 1) % k + 1])
+    G = pkt.build_csr(dev(src), dev(dst), k + 1)
+    for loop in (pkt.LOOP_PLAIN, pkt.LOOP_PERSISTENT):
+        assert np.all(host(G.decompose(loop=loop)) == 3)
+
+
+def _fig3_cases():
+    rows = [ln for ln in open(os.path.join(GOLD, "fig3_states.txt")).read().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    out = []
+    for r in rows:
+        f = [x.strip() for x in r.split(";")]
+        ints = lambda s: [] if s == "-" else [int(x) for x in s.split()]
+        out.append((int(f[0]), ints(f[1]), ints(f[2]), ints(f[3]), ints(f[4]), ints(f[5])))
+    return out
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("case", _fig3_cases())
+def test_fig3_sublevel_states(pkt, case, variant):
+    """Fig. 3: one ProcessSubLevel on hand-set states of one triangle."""
+    import torch
+
+    l, S, proc, curr, S_after, nxt = case
+    G = pkt.build_csr(dev([0, 0, 1]), dev([1, 2, 2]), 3, degree_order=False)
+    dS = dev(S)
+    flags = torch.tensor(proc, dtype=torch.uint8, device="cuda") * pkt.PROCESSED
+    got = G.peel_sublevel(dS, flags, dev(curr), l, variant=_var(pkt, variant))
+    assert host(dS).tolist() == S_after
+    assert sorted(host(got).tolist()) == nxt
+    fl = host(flags)
+    for e in curr:
+        assert fl[e] == pkt.PROCESSED
+    for e in nxt:
+        assert fl[e] & pkt.IN_CURR
+
+
+def test_sublevel_states_on_larger_graph(pkt):
+    """Every sub-level of a real run, replayed one at a time through the
+    state-level entry point with relabelling on, against the oracle's."""
+    import torch
+
+    g = gg.chung_lu(1500, 2.1, 14.0, 300.0, seed=31)
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, degree_order=True)
+    S = oracle.support(g.n, eu, ev).copy()
+    flags = np.zeros(eu.size, np.uint8)
+    dS = dev(S)
+    dF = torch.zeros(eu.size, dtype=torch.uint8, device="cuda")
+    todo, l, steps = eu.size, 0, 0
+    while todo > 0:
+        curr = np.nonzero((S == l) & (flags & oracle.PROCESSED == 0))[0].astype(np.int32)
+        while curr.size:
+            todo -= curr.size
+            want_next = oracle.sublevel(g.n, eu, ev, S, flags, curr, l)
+            dF[torch.from_numpy(curr).long().cuda()] |= pkt.IN_CURR
+            got_next = G.peel_sublevel(dS, dF, dev(curr), l, variant=steps % 3 - 1)
+            assert np.array_equal(np.sort(host(got_next)), want_next)
+            assert np.array_equal(host(dS), S)
+            assert np.array_equal(host(dF), flags)
+            curr = want_next
+            steps += 1
+        l += 1
+
+
+# ----------------------------------------------------------------- edge cases
+
+def test_empty_and_degenerate_inputs(pkt):
+    import torch
+
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    for n in (0, 1, 10):
+        G = pkt.build_csr(e, e, n)
+        assert G.m == 0 and G.decompose().numel() == 0 and G.support().numel() == 0
+    # only self-loops and repeats of one edge
+    G = pkt.build_csr(dev([3, 3, 1, 2, 2, 1]), dev([3, 3, 2, 1, 1, 2]), 5)
+    assert G.m == 1 and host(G.decompose()).tolist() == [2]
+    # isolated vertices around a triangle, both orientations, repeats
+    G = pkt.build_csr(dev([7, 9, 9, 8, 7]), dev([9, 8, 7, 7, 8]), 20)
+    assert host(G.decompose()).tolist() == [3, 3, 3]
+    u, v = G.edge_list()
+    assert host(u).tolist() == [7, 7, 8] and host(v).tolist() == [8, 9, 9]
+
+
+def test_bad_ids_are_rejected(pkt):
+    with pytest.raises(pkt.TrussError) as ex:
+        pkt.build_csr(dev([0, 1]), dev([1, 5]), 5)
+    assert ex.value.status == pkt.EBADGRAPH
+    with pytest.raises(pkt.TrussError) as ex:
+        pkt.build_csr(dev([0, -1]), dev([1, 2]), 5)
+    assert ex.value.status == pkt.EBADGRAPH
+
+
+def test_barrier_wait_limit_returns_status(pkt):
+    """A grid-barrier wait that runs past its limit ends the kernel with
+    TRUSS_ETIMEOUT (here the limit is 1 ns, so the first wait runs out); the
+    context stays usable and the next call is exact."""
+    g = gg.workload("rmat10_ef8")
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    with pytest.raises(pkt.TrussError) as ex:
+        G.decompose(loop=pkt.LOOP_PERSISTENT, timeout_ns=1)
+    assert ex.value.status == pkt.ETIMEOUT
+    tau = G.decompose(loop=pkt.LOOP_PERSISTENT)
+    assert np.array_equal(host(tau), oracle.truss_of_edges(g.n, g.src, g.dst)[2])
+
+
+def test_host_buffer_pipeline(pkt):
+    for name, g in SMALL[:3]:
+        tau, st = pkt.decompose_host(g.src, g.dst, g.n)
+        assert np.array_equal(tau, oracle.truss_of_edges(g.n, g.src, g.dst)[2])
+        assert st["m"] == tau.size
+
+
+def test_stats(pkt):
+    g = gg.workload("rmat10_ef8")
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    tau, st = G.decompose(stats=True)
+    eu, ev, want = oracle.truss_of_edges(g.n, g.src, g.dst)
+    S0 = oracle.support(g.n, eu, ev)
+    assert st["triangles"] * 3 == int(S0.sum())
+    assert st["t_max"] == int(want.max())
+    assert st["m"] == eu.size
+    _, lv, sz = oracle.pkt_serial(g.n, eu, ev)
+    assert st["sublevels"] == sz.size and st["levels"] == np.unique(lv).size
