@@ -37,8 +37,8 @@
 namespace {
 
 enum {
-    C_CNT = 0,   // [0..3] frontier size of sub-level g in slot g & 3
-    C_MIN = 4,   // [4..6] minimum live support above l, slot = scan number % 3
+    C_CNT = 0,   // [0..3] frontier size produced by phase p, slot p & 3
+    C_MIN = 4,   // [4..7] minimum live support above l found by phase p, slot p & 3
     C_BAR_COUNT = 8,
     C_BAR_GEN = 9,
     C_ERR = 10,
@@ -297,15 +297,23 @@ __global__ void __launch_bounds__(PT)
     __syncthreads();
     const unsigned nblocks = gridDim.x;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    // Phase p (every Scan and every sub-level is one phase) writes its
+    // counters to slot p & 3.  Slot (p+2) & 3 is cleared during phase p: its
+    // last readers read it right after the barrier that ended phase p-2, and
+    // the barrier ending phase p-1 lies in between.
     int32_t l = 0, g = 0;
-    int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0;
+    int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0, p = 0;
     while (processed < G.m) {
-        if (leader) ctr[C_MIN + (int)((sc + 1) % 3)] = INT_MAX;
+        if (leader) {
+            ctr[C_CNT + ((p + 2) & 3)] = 0;
+            ctr[C_MIN + ((p + 2) & 3)] = INT_MAX;
+        }
         int32_t* curr = (g & 1) ? fr1 : fr0;
-        scan_level(G.ss, G.m, l, g, curr, ctr + C_CNT + (g & 3), ctr + C_MIN + (int)(sc % 3));
+        scan_level(G.ss, G.m, l, g, curr, ctr + C_CNT + (p & 3), ctr + C_MIN + (p & 3));
         if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-        int c = ld_acquire_gpu(ctr + C_CNT + (g & 3));
-        const int mn = ld_acquire_gpu(ctr + C_MIN + (int)(sc % 3));
+        int c = ld_acquire_gpu(ctr + C_CNT + (p & 3));
+        const int mn = ld_acquire_gpu(ctr + C_MIN + (p & 3));
+        p++;
         sc++;
         if (c == 0) {
             if (mn == INT_MAX) break;
@@ -320,14 +328,15 @@ __global__ void __launch_bounds__(PT)
                     rec_level[nsub] = l;
                     rec_size[nsub] = c;
                 }
-                ctr[C_CNT + ((g + 2) & 3)] = 0;
+                ctr[C_CNT + ((p + 2) & 3)] = 0;
+                ctr[C_MIN + ((p + 2) & 3)] = INT_MAX;
             }
             int32_t* cu = (g & 1) ? fr1 : fr0;
             int32_t* nx = (g & 1) ? fr0 : fr1;
-            process_frontier<Off>(G, cu, c, l, g, nx, ctr + C_CNT + ((g + 1) & 3), variant, thr_thread, thr_block,
-                                  &sm);
+            process_frontier<Off>(G, cu, c, l, g, nx, ctr + C_CNT + (p & 3), variant, thr_thread, thr_block, &sm);
             if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-            c = ld_acquire_gpu(ctr + C_CNT + ((g + 1) & 3));
+            c = ld_acquire_gpu(ctr + C_CNT + (p & 3));
+            p++;
             g++;
             nsub++;
         }
@@ -368,7 +377,7 @@ __global__ void k_sum_support(const int2* __restrict__ ss, int64_t m, unsigned l
 
 __global__ void k_init_counters(int* ctr) {
     int i = threadIdx.x;
-    if (i < C_TOTAL) ctr[i] = (i >= C_MIN && i < C_MIN + 3) ? INT_MAX : 0;
+    if (i < C_TOTAL) ctr[i] = (i >= C_MIN && i < C_MIN + 4) ? INT_MAX : 0;
 }
 
 // state import for truss_peel_sublevel: canonical (S, flags) -> internal ss
