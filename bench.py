@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: edges/s of a full truss decomposition (support + peeling) on a
+device-resident graph, one JSON line on stdout.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+A step is one whole decomposition: support (Algorithm 3) and the level loop
+(Algorithms 4-5) over the Chung-Lu power-law workload (2^20 vertices,
+exponent 2.1, mean degree 20, expected degrees clipped at 2^14, seed 2),
+with the CSR already in HBM.  Every step is timed with CUDA events on the
+stream the library launches on; L2 is flushed (a 256 MiB write) between
+steps, outside the timed events.  Under torchrun each rank runs its own
+replica on its own GPU (the decomposition does not shard) and
+the line reports the sum of edges over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s of full truss decomposition + % HBM peak; persistent+learned vs plain"
+UNIT = "edges/s"
+WORKLOAD = "chunglu_n2^20_d20"
+WORKLOAD_DESC = ("Chung-Lu power-law graph, 2^20 vertices, degree exponent 2.1, mean degree 20, "
+                 "max expected degree 2^14, seed 2, int32 CSR + int32 Eid/support")
+# bounded CPU sample of the same generator family for the oracle timings
+CPU_SAMPLE = dict(n=1 << 17, gamma=2.1, mean_deg=20.0, max_deg=float(1 << 14), seed=2)
+CPU_SAMPLE_DESC = ("oracle (serial Algorithm 1 peel, 1 core) on a Chung-Lu sample of the same family: "
+                   "2^17 vertices, exponent 2.1, mean degree 20, max expected degree 2^14, seed 2")
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline model
+
+def algorithmic_bytes(st, n):
+    """Compulsory bytes of each phase, from exact work counts (the design doc,
+    "Algorithmic bytes"): support = 32m + 8n + 4W+ + 12T; peeling =
+    8m per Scan + 36m + 4 sum_e min(d(u), d(v)) + 28T."""
+    m, T = st["m"], st["triangles"]
+    sup = 32 * m + 8 * n + 4 * st["wedges_up"] + 12 * T
+    peel = 8 * m * st["scans"] + 36 * m + 4 * st["dmin_sum"] + 28 * T
+    return sup, peel
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1707_02000_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload, {}).get(kernel)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def peaks():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def cpu_sample_graph():
+    import graphgen as gg
+    return gg.chung_lu(CPU_SAMPLE["n"], CPU_SAMPLE["gamma"], CPU_SAMPLE["mean_deg"], CPU_SAMPLE["max_deg"],
+                       CPU_SAMPLE["seed"])
+
+
+def time_oracle_once(g):
+    import oracle
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    t0 = time.perf_counter()
+    oracle.truss(g.n, eu, ev)
+    return eu.size, time.perf_counter() - t0
+
+
+def cpu_baseline():
+    g = cpu_sample_graph()
+    m, dt = time_oracle_once(g)
+    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_DESC}; m={m}, {dt:.2f} s"}
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    g = cpu_sample_graph()
+    times = []
+    m = 0
+    for i in range(args.warmup + args.steps):
+        m, dt = time_oracle_once(g)
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    v = m * len(times) / total
+    emit({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+          "warmup": args.warmup, "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+          "config": {"workload": f"{args.workload}: {WORKLOAD_DESC}",
+                     "sample": f"each step: {CPU_SAMPLE_DESC}", "m_sample": m},
+          "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE_DESC},
+          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_1707_02000_gb300 as pkt
+
+    ws, rank, local = dist_info()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    g = gg.workload(args.workload)
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    G = pkt.build_csr(src, dst, g.n)
+    m = G.m
+    out = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    loop = {"persistent": pkt.LOOP_PERSISTENT, "plain": pkt.LOOP_PLAIN}[args.loop]
+    stream = torch.cuda.current_stream()
+
+    def timed(loop_form, steps, warmup):
+        for _ in range(warmup):
+            G.decompose(out=out, loop=loop_form, sync=True, stats=True)
+        barrier()
+        per, stats = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = G.decompose(out=out, loop=loop_form, sync=True, stats=True)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+            stats.append(st)
+        barrier()
+        return per, stats
+
+    with ClockSampler(local) as clk:
+        per, stats = timed(loop, args.steps, args.warmup)
+    total_ms = sum(per)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = m * args.steps * ws / (total_ms / 1000.0)
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
+    st0 = stats[-1]
+    res["config"] = {"workload": f"{args.workload}: {WORKLOAD_DESC}", "m": m, "n": g.n,
+                     "loop": args.loop, "variant": "per-edge heuristic", "vertex_order": "degree",
+                     "l2": "flushed between steps (256 MiB write, untimed)", "replicas": ws,
+                     "triangles": st0["triangles"], "t_max": st0["t_max"], "sublevels": st0["sublevels"],
+                     "scans": st0["scans"]}
+    res["gpu_launches"] = int(sum(s["launches"] for s in stats))
+    res["clocks"] = clk.summary()
+
+    # roofline: the phase that takes longer, bytes from exact work counts
+    ms_sup = statistics.mean(s["ms_support"] for s in stats)
+    ms_peel = statistics.mean(s["ms_peel"] for s in stats)
+    b_sup, b_peel = algorithmic_bytes(st0, g.n)
+    peak, peak_kind = peaks()
+    if ms_peel >= ms_sup:
+        kname, b, ms = ("k_persistent" if args.loop == "persistent" else "k_process"), b_peel, ms_peel
+    else:
+        kname, b, ms = "k_support_warp", b_sup, ms_sup
+    ach = b / (ms / 1000.0) / 1e9
+    res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                       "traffic": recorded_traffic(kname, args.workload), "kernel": kname,
+                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                       else "fallback 6.8 TB/s",
+                       "phases_ms": {"support": ms_sup, "peel": ms_peel},
+                       "algorithmic_bytes": {"support": b_sup, "peel": b_peel}}
+
+    if not args.no_plain and args.loop != "plain":
+        pper, pstats = timed(pkt.LOOP_PLAIN, max(1, min(args.steps, 5)), 1)
+        pv = m / (statistics.mean(pper) / 1000.0) * ws
+        res["plain"] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pper),
+                        "speedup_of_reported_form": value / pv,
+                        "launches_per_step": int(statistics.mean(s["launches"] for s in pstats))}
+
+    if not args.no_e2e:
+        # the public host-buffer entry point: H2D of the raw edge list from
+        # pinned memory, device build, support + peel, D2H of the trussness
+        hs = torch.from_numpy(g.src).pin_memory()
+        hd = torch.from_numpy(g.dst).pin_memory()
+        ho = torch.empty(g.n_in, dtype=torch.int32).pin_memory()
+        hs_np, hd_np, ho_np = hs.numpy(), hd.numpy(), ho.numpy()
+        pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop)
+        barrier()
+        k = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            tau, _ = pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / k
+        res["e2e"] = {"value": m / dt * ws, "unit": UNIT, "h2d_bytes_per_step": int(8 * g.n_in),
+                      "d2h_bytes_per_step": int(4 * m), "ms_per_step": dt * 1000,
+                      "includes": "H2D of raw pairs, device CSR build, support, peel, D2H of trussness"}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        emit(res)
+    G.free()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--loop", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -126,11 +126,14 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 #define TRUSS_LOOP_PERSISTENT 1 /* one cooperative kernel, grid barriers with
                                    a time limit between phases            */
 
-/* ProcessSubLevel kernel variants (all exact) */
-#define TRUSS_VAR_AUTO (-1)   /* per-edge choice by the built-in heuristic   */
-#define TRUSS_VAR_THREAD 0    /* one thread per frontier edge               */
-#define TRUSS_VAR_WARP 1      /* one warp per frontier edge                 */
-#define TRUSS_VAR_BLOCK 2     /* one thread block per frontier edge         */
+/* ProcessSubLevel work mappings (all exact).  Frontier edges whose shorter
+ * adjacency row has more than 32 entries are always cut into fixed-size
+ * chunks shared by every warp of the grid; the variant chooses how many
+ * lanes walk each of the other ("light") edges. */
+#define TRUSS_VAR_AUTO (-1)   /* chosen per sub-level from the frontier size */
+#define TRUSS_VAR_THREAD 0    /* one thread per light edge                   */
+#define TRUSS_VAR_GROUP 1     /* eight lanes per light edge                  */
+#define TRUSS_VAR_WARP 2      /* one warp per light edge                     */
 
 typedef struct truss_opts {
     int32_t loop;        /* TRUSS_LOOP_*                                      */
@@ -144,7 +147,11 @@ typedef struct truss_opts {
     int32_t* h_sub_level; /* optional host arrays: level l and frontier size */
     int64_t* h_sub_size;  /* |curr| of every non-empty sub-level, in order   */
     int64_t max_sub;      /* their capacity (entries); needs sync = 1        */
-    int32_t reserved[8];
+    int32_t* d_peel_step; /* optional device int32[m], canonical order: the
+                             number of the sub-level (0, 1, ...) in which each
+                             edge was peeled -- a peeling order that lets a
+                             checker certify the result (see truss_decompose) */
+    int32_t reserved[6];
 } truss_opts;
 
 typedef struct truss_stats {
@@ -156,7 +163,12 @@ typedef struct truss_stats {
     int32_t levels;      /* levels with at least one edge                    */
     float ms_support;    /* device time of the support phase (sync = 1)      */
     float ms_peel;       /* device time of the peeling phase (sync = 1)      */
-    int64_t reserved[6];
+    int64_t launches;    /* kernels this call launched                        */
+    int64_t wedges_up;   /* W+ = sum over v of d-(v) * d+(v): N+ entries the
+                            support kernel reads (internal vertex order)      */
+    int64_t dmin_sum;    /* sum over edges of min(d(u), d(v)): entries of the
+                            shorter row that ProcessSubLevel reads            */
+    int64_t reserved[3];
 } truss_stats;
 
 /* Fill *opts with defaults: persistent loop, heuristic variants, no sync,
@@ -174,6 +186,11 @@ TRUSS_API void truss_default_opts(truss_opts* opts);
  * handles it (§III, Fig. 3).  Trussness = final support + 2.
  *   d_truss : device int32[m], canonical order (written).
  *   opts    : NULL for defaults (truss_default_opts).
+ * Certificate: with opts->d_peel_step, ordering the edges by (peel step,
+ * edge id) gives a removal order in which every edge, when removed, lies in
+ * at most trussness-2 triangles of the edges not yet removed, and trussness
+ * never decreases along it; together with "every edge of trussness k lies in
+ * >= k-2 triangles of edges of trussness >= k" this proves the result exact.
  *   stats   : may be NULL; filled only when opts->sync is set.
  */
 TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts* opts, truss_stats* stats, void* stream);

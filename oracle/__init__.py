@@ -52,12 +52,14 @@ def bind(path: str):
     lib.or_support.restype = ctypes.c_int
     lib.or_truss_wc.argtypes = [I32, I64, i32p, i32p, i32p, i32p]
     lib.or_truss_wc.restype = ctypes.c_int
-    lib.or_pkt_serial.argtypes = [I32, I64, i32p, i32p, i32p, i32p, i64p, I64]
+    lib.or_pkt_serial.argtypes = [I32, I64, i32p, i32p, i32p, i32p, i64p, I64, i32p]
     lib.or_pkt_serial.restype = I64
     lib.or_sublevel.argtypes = [I32, I64, i32p, i32p, i32p, u8p, i32p, I64, I32, i32p]
     lib.or_sublevel.restype = I64
     lib.or_truss_batch.argtypes = [I64, i32p, i64p, i32p, i32p, i64p, i32p, ctypes.c_int]
     lib.or_truss_batch.restype = ctypes.c_int
+    lib.or_certify.argtypes = [I32, I64, i32p, i32p, i32p, i32p, ctypes.c_int, i64p]
+    lib.or_certify.restype = I64
     return lib
 
 
@@ -133,23 +135,44 @@ def truss_of_edges(n: int, src, dst):
     return eu, ev, truss(n, eu, ev)
 
 
-def pkt_serial(n: int, eu, ev, max_sub: int = 1 << 20):
+def pkt_serial(n: int, eu, ev, max_sub: int = 1 << 20, return_steps: bool = False):
     """Algorithm 4 with Algorithm 5, one edge at a time.  Returns
     ``(tau, sub_levels, sub_sizes)``: trussness and, per non-empty sub-level,
-    its level l and frontier size |curr|."""
+    its level l and frontier size |curr|; with ``return_steps`` also the
+    sub-level number each edge was peeled in."""
     lib = _load()
     eu, up = _i32(eu)
     ev, vp = _i32(ev)
     m = eu.shape[0]
     tau = np.empty(max(m, 1), np.int32)
+    step = np.empty(max(m, 1), np.int32)
     lv = np.empty(max_sub, np.int32)
     sz = np.empty(max_sub, np.int64)
     ns = lib.or_pkt_serial(n, m, up, vp, _i32(tau)[1], _i32(lv)[1],
-                           sz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), max_sub)
+                           sz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), max_sub, _i32(step)[1])
     _check(ns, "pkt_serial")
     if ns > max_sub:
         raise ValueError("more sub-levels than max_sub")
+    if return_steps:
+        return tau[:m], lv[:ns].copy(), sz[:ns].copy(), step[:m].copy()
     return tau[:m], lv[:ns].copy(), sz[:ns].copy()
+
+
+def certify(n: int, eu, ev, tau, step, nthreads: int | None = None):
+    """Check a claimed trussness with its claimed peeling order against the
+    definition (see or_certify).  Returns ``(violations, first_bad_edge)``;
+    zero violations proves the claim exact."""
+    lib = _load()
+    eu, up = _i32(eu)
+    ev, vp = _i32(ev)
+    tau, tp = _i32(tau)
+    step, sp = _i32(step)
+    fb = ctypes.c_int64()
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    r = lib.or_certify(n, eu.shape[0], up, vp, tp, sp, nthreads, ctypes.byref(fb))
+    _check(r, "certify")
+    return int(r), int(fb.value)
 
 
 def sublevel(n: int, eu, ev, S, flags, curr, l: int):

@@ -33,6 +33,20 @@
  *                     state (S, processed/inCurr flags, curr, l).
  *   or_truss_batch    or_truss_wc over many independent graphs, spread over
  *                     host threads (one graph per task).
+ *   or_certify        checks a claimed trussness against the definition at
+ *                     any size, given a claimed peeling order (the sub-level
+ *                     each edge was peeled in).  Lower bound: every edge of
+ *                     claimed trussness k lies in >= k-2 triangles whose
+ *                     other edges have claimed trussness >= k, so each set
+ *                     {claimed >= k} is a k-truss subgraph (§II) and the true
+ *                     trussness is at least the claim.  Upper bound: ordering
+ *                     edges by (step, id), the claim never decreases along
+ *                     the order and every edge lies in <= claim-2 triangles
+ *                     of edges after it; if e were in a k-truss H with
+ *                     k > claim(e), the first edge of H in the order would
+ *                     lie in >= k-2 triangles of later edges while its own
+ *                     claim is <= claim(e) < k -- a contradiction.  Edges
+ *                     are checked in parallel on host threads.
  *
  * Readings of the paper taken here (each is stated where it is used):
  *   - the level variable l of Algorithms 4 and 5 is a support value, so
@@ -324,9 +338,10 @@ int64_t or_sublevel(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, 
 
 /* Algorithm 4 run serially.  tau: trussness per edge.  sub_level/sub_size:
  * level and frontier size of each non-empty sub-level, written up to
- * max_sub entries; the return value is the total number of sub-levels. */
+ * max_sub entries; the return value is the total number of sub-levels.
+ * step (may be NULL): number of the sub-level each edge was peeled in. */
 int64_t or_pkt_serial(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, int32_t* tau,
-                      int32_t* sub_level, int64_t* sub_size, int64_t max_sub) {
+                      int32_t* sub_level, int64_t* sub_size, int64_t max_sub, int32_t* step) {
     if (m < 0 || m > INT32_MAX - 1) return -1;
     graph_t g;
     int rc = graph_build(&g, n, m, eu, ev);
@@ -349,6 +364,8 @@ int64_t or_pkt_serial(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev
             if (S[e] == l && !(flag[e] & F_PROCESSED)) { curr[ncurr++] = (int32_t)e; flag[e] |= F_INCURR; }
         while (ncurr > 0) {
             if (nsub < max_sub) { sub_level[nsub] = l; sub_size[nsub] = ncurr; }
+            if (step)
+                for (int64_t c = 0; c < ncurr; c++) step[curr[c]] = (int32_t)nsub;
             nsub++;
             todo -= ncurr;
             int64_t nn = sublevel(&g, eu, ev, S, flag, curr, ncurr, l, next);
@@ -410,4 +427,103 @@ int or_truss_batch(int64_t G, const int32_t* nverts, const int64_t* eoff, const 
     for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, batch_worker, &c);
     for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
     return atomic_load(&c.err);
+}
+
+/* ------------------------------------------------------ result certificate */
+
+typedef struct {
+    const graph_t* g;
+    const int32_t *eu, *ev, *tau, *step;
+    int64_t m;
+    atomic_llong next_chunk;
+    atomic_llong violations;
+    int64_t first_bad;  /* smallest violating edge id found (or -1) */
+    pthread_mutex_t lock;
+} cert_ctx;
+
+/* key order (step, id) */
+static inline int later(const cert_ctx* c, int32_t f, int32_t e) {
+    return c->step[f] > c->step[e] || (c->step[f] == c->step[e] && f > e);
+}
+
+static void* cert_worker(void* p) {
+    cert_ctx* c = (cert_ctx*)p;
+    const graph_t* g = c->g;
+    const int64_t CH = 4096;
+    for (;;) {
+        int64_t lo = atomic_fetch_add(&c->next_chunk, CH);
+        if (lo >= c->m) break;
+        int64_t hi = lo + CH < c->m ? lo + CH : c->m;
+        for (int64_t e = lo; e < hi; e++) {
+            int32_t u = c->eu[e], v = c->ev[e];
+            int32_t a = deg(g, u) <= deg(g, v) ? u : v, b = a == u ? v : u;
+            int32_t k = c->tau[e];
+            int64_t ge = 0, lat = 0;
+            for (int64_t j = g->off[a]; j < g->off[a + 1]; j++) {
+                int32_t w = g->adj[j].w;
+                if (w == b) continue;
+                int32_t f = g->adj[j].e, h = find_edge(g, b, w);
+                if (h < 0) continue;
+                if (c->tau[f] >= k && c->tau[h] >= k) ge++;
+                if (later(c, f, (int32_t)e) && later(c, h, (int32_t)e)) lat++;
+            }
+            if (k < 2 || ge < k - 2 || lat > k - 2) {
+                atomic_fetch_add(&c->violations, 1);
+                pthread_mutex_lock(&c->lock);
+                if (c->first_bad < 0 || e < c->first_bad) c->first_bad = e;
+                pthread_mutex_unlock(&c->lock);
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Returns the number of violating edges (0: the claim is exactly the
+ * trussness), or -1 / -2 on bad arguments / allocation failure.  *first_bad
+ * receives the smallest violating edge id, or -1. */
+int64_t or_certify(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, const int32_t* tau,
+                   const int32_t* step, int nthreads, int64_t* first_bad) {
+    if (m < 0 || m > INT32_MAX - 1) return -1;
+    *first_bad = -1;
+    graph_t g;
+    int rc = graph_build(&g, n, m, eu, ev);
+    if (rc) return rc;
+    int64_t bad = 0;
+    /* the claim must not decrease along the (step, id) order: per step,
+     * claims are compared across consecutive steps in step order */
+    int32_t smax = -1;
+    for (int64_t e = 0; e < m; e++) {
+        if (step[e] < 0) { graph_free(&g); return -1; }
+        if (step[e] > smax) smax = step[e];
+    }
+    int32_t* lo_t = malloc(sizeof(int32_t) * ((size_t)smax + 2));
+    int32_t* hi_t = malloc(sizeof(int32_t) * ((size_t)smax + 2));
+    if (!lo_t || !hi_t) { free(lo_t); free(hi_t); graph_free(&g); return -2; }
+    for (int32_t s = 0; s <= smax; s++) { lo_t[s] = INT32_MAX; hi_t[s] = INT32_MIN; }
+    for (int64_t e = 0; e < m; e++) {
+        if (tau[e] < lo_t[step[e]]) lo_t[step[e]] = tau[e];
+        if (tau[e] > hi_t[step[e]]) hi_t[step[e]] = tau[e];
+    }
+    int32_t run = INT32_MIN;
+    for (int32_t s = 0; s <= smax; s++) {
+        if (lo_t[s] == INT32_MAX) continue;
+        if (lo_t[s] != hi_t[s] || lo_t[s] < run) bad++;
+        run = hi_t[s];
+    }
+    free(lo_t);
+    free(hi_t);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    cert_ctx c;
+    c.g = &g; c.eu = eu; c.ev = ev; c.tau = tau; c.step = step; c.m = m; c.first_bad = -1;
+    atomic_init(&c.next_chunk, 0);
+    atomic_init(&c.violations, 0);
+    pthread_mutex_init(&c.lock, NULL);
+    pthread_t th[256];
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, cert_worker, &c);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    pthread_mutex_destroy(&c.lock);
+    graph_free(&g);
+    *first_bad = c.first_bad;
+    return bad + (int64_t)atomic_load(&c.violations);
 }

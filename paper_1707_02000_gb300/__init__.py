@@ -27,7 +27,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP = -1, -2
 DEGREE_ORDER = 1
 OFFSETS64 = 2
 LOOP_PLAIN, LOOP_PERSISTENT = 0, 1
-VAR_AUTO, VAR_THREAD, VAR_WARP, VAR_BLOCK = -1, 0, 1, 2
+VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP = -1, 0, 1, 2
 PROCESSED, IN_CURR = 1, 2
 
 # Every symbol include/truss.h declares (checked by the tests).
@@ -48,13 +48,15 @@ class Opts(ctypes.Structure):
     _fields_ = [("loop", ctypes.c_int32), ("variant", ctypes.c_int32), ("sync", ctypes.c_int32),
                 ("level_jump", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("h_sub_level", ctypes.POINTER(ctypes.c_int32)), ("h_sub_size", ctypes.POINTER(ctypes.c_int64)),
-                ("max_sub", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+                ("max_sub", ctypes.c_int64), ("d_peel_step", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("sublevels", ctypes.c_int64), ("scans", ctypes.c_int64),
                 ("triangles", ctypes.c_int64), ("t_max", ctypes.c_int32), ("levels", ctypes.c_int32),
-                ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("reserved", ctypes.c_int64 * 6)]
+                ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("launches", ctypes.c_int64),
+                ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -185,13 +187,17 @@ class Graph:
         return out
 
     def decompose(self, out=None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, sync=True, level_jump=True,
-                  timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False):
+                  timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False,
+                  peel_step=None):
         """Trussness (int32[m], canonical order).  With ``record`` also
         returns the (level, |curr|) of every sub-level; with ``stats`` a
-        dict of run statistics."""
+        dict of run statistics; ``peel_step`` (a CUDA int32[m] tensor)
+        receives the sub-level each edge was peeled in."""
         out = self._empty(self.m) if out is None else out
         o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record)),
                          level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
+        if peel_step is not None and self.m:
+            o.d_peel_step = peel_step.data_ptr()
         rl = rs = None
         if record:
             rl = np.zeros(max_sub, np.int32)

@@ -11,16 +11,23 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "graph.cuh"
 #include "prims.cuh"
+
+#include <algorithm>
 
 using prims::talloc;
 using prims::tfree;
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void truss_note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+static std::atomic<long long> g_launches{0};
+void truss_note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long truss_launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char* truss_strerror(int status) {
     switch (status) {
@@ -180,6 +187,24 @@ __global__ void k_classify_vertices(const int64_t* __restrict__ rowptr, const in
     }
 }
 
+// W+ = sum_v d-(v) d+(v) and sum over edges of min(d(u), d(v)).
+__global__ void k_work_stats(const int64_t* __restrict__ rowptr, const int64_t* __restrict__ eo, int32_t n,
+                             const int2* __restrict__ el, int64_t m, unsigned long long* __restrict__ out) {
+    unsigned long long w = 0, d = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        w += (unsigned long long)(eo[u] - rowptr[u]) * (unsigned long long)(rowptr[u + 1] - eo[u]);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        int2 xy = el[e];
+        d += (unsigned long long)min(rowptr[xy.x + 1] - rowptr[xy.x], rowptr[xy.y + 1] - rowptr[xy.y]);
+    }
+    w = warp_sum(w);
+    d = warp_sum(d);
+    if (lane_id() == 0) {
+        atomicAdd(out, w);
+        atomicAdd(out + 1, d);
+    }
+}
+
 struct Csr64 {
     int64_t* rowptr = nullptr;
     int64_t* eo = nullptr;
@@ -318,6 +343,20 @@ int build_impl(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t
         k_narrow<int32_t><<<grid_for((int64_t)n + 1, B), B, 0, s>>>(c1.rowptr, (int64_t)n + 1, (int32_t*)g->rowptr);
         if (n > 0) k_narrow<int32_t><<<grid_for(n, B), B, 0, s>>>(c1.eo, n, (int32_t*)g->eo);
         CU(cudaGetLastError());
+    }
+    // work statistics (reported by truss_decompose)
+    {
+        unsigned long long* ws = nullptr;
+        CU(talloc(&ws, 2, s));
+        CU(cudaMemsetAsync(ws, 0, 2 * sizeof(unsigned long long), s));
+        k_work_stats<<<grid_for(std::max<int64_t>(n, m), B), B, 0, s>>>(c1.rowptr, c1.eo, n, g->el, m, ws);
+        CU(cudaGetLastError());
+        unsigned long long h[2];
+        CU(cudaMemcpyAsync(h, ws, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        g->wedges_up = (int64_t)h[0];
+        g->dmin_sum = (int64_t)h[1];
+        tfree(ws, s);
     }
     // vertex classes for the support kernels
     {

@@ -11,6 +11,9 @@
 // Return a TRUSS_ECUDA status from a host function when a CUDA call fails,
 // remembering the CUDA error for truss_strerror / truss_last_cuda_error.
 void truss_note_cuda_error(cudaError_t e);
+// Process-wide count of kernels this library has launched (stats only).
+void truss_note_launch(int k = 1);
+long long truss_launch_count();
 #define CU(call)                                   \
     do {                                           \
         cudaError_t e_ = (call);                   \

@@ -19,7 +19,11 @@
 //                     <=> stamp == g (the processed / inCurr / inNext arrays
 //                     of Algorithms 4-5 folded into one word, so finishing a
 //                     sub-level needs no pass over curr: g+1 flips them all).
-//   fr[2]  int32[m]   curr / next frontiers (ping-pong)
+//   dmin   int32[m]   min(d(u), d(v)) of each edge: length of the shorter
+//                     row ProcessSubLevel walks, which sets its light/heavy
+//                     class
+//   fq[2]  3 x int32[m] per side of the curr/next ping-pong: light edges,
+//                     heavy edges, first chunk number of each heavy edge
 //   ctr    int[...]   device counters (see peel.cu)
 #pragma once
 #include "common.cuh"
@@ -51,9 +55,13 @@ struct truss_graph {
     int32_t n_sup_huge = 0;
     int64_t max_deg = 0;
     int64_t max_updeg = 0;
+    int64_t wedges_up = 0;  // sum_v d-(v) d+(v)
+    int64_t dmin_sum = 0;   // sum_e min(d(u), d(v))
+    int hc = 64;            // heavy-edge chunk length used by ProcessSubLevel
     // peeling workspace
     int2* ss = nullptr;
-    int32_t* fr[2] = {nullptr, nullptr};
+    int32_t* dmin = nullptr;
+    int32_t* fq[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int* ctr = nullptr;
     int* h_ctr = nullptr;  // pinned host mirror
     int latched = 0;       // latched device-side error status

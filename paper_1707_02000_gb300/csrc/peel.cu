@@ -1,27 +1,32 @@
 // Level-synchronous peeling (Algorithms 4 and 5, §III) on the device.
 //
 // Scan (K2): one coalesced pass over the {S, stamp} words, 16 bytes (two
-// edges) per thread per step; edges with S = l join curr (warp ballot +
-// one atomic per warp), and the minimum support above l is reduced on the
-// side so that an empty level can jump straight to the next live one.
+// edges) per thread per step; edges with S = l join curr (warp ballot + one
+// atomic per warp), and the minimum support above l is reduced on the side
+// so that an empty level can jump straight to the next live one.
 //
-// ProcessSubLevel (K3): for every e1 = {u, v} in curr, the common
-// neighbours w of u and v are found by binary search of each entry of the
-// shorter row in the longer one.  Each triangle {e1, e2, e3} whose other two
-// edges are unprocessed lowers e2 (resp. e3) by one when its support is
-// above l and e3 (resp. e2) is not in curr or has a larger id than e1: the
-// two-sided reading of Algorithm 5, which prints only the e2 case.  The
-// decrement is atomicSub; an edge whose old value was l+1 joins next; a
-// thread that pushed an edge below l adds the 1 back (the clamp-and-restore
-// of Algorithm 5), so the final value is max(l, S - #triangles removed).
-// The rule is symmetric in e2 and e3, so which of them is {u,w} or {v,w}
-// does not matter.
+// ProcessSubLevel (K3): for every e1 = {u, v} in curr, the common neighbours
+// w of u and v are found by binary search of each entry of the shorter row in
+// the longer one.  Each triangle {e1, e2, e3} whose other two edges are
+// unprocessed lowers e2 (resp. e3) by one when its support is above l and e3
+// (resp. e2) is not in curr or has a larger id than e1: the two-sided reading
+// of Algorithm 5, which prints only the e2 case.  The decrement is atomicSub;
+// an edge whose old value was l+1 joins next; a thread that pushed an edge
+// below l adds the 1 back (the clamp-and-restore of Algorithm 5), so the
+// final value is max(l, S - #triangles removed).  The rule is symmetric in e2
+// and e3, so which of them is {u,w} or {v,w} does not matter.
 //
-// Three ways to map a frontier edge onto the GPU, all exact:
-//   thread  one thread walks the shorter row (short rows),
-//   warp    32 lanes split the shorter row (the common case),
-//   block   the whole block splits it (hubs).
-// The default picks per edge by the length of the shorter row.
+// Work mapping.  A frontier is kept as two lists:
+//   light  edges whose shorter row has <= LIGHT entries; each is walked by a
+//          group of G lanes, G in {1, 8, 32} chosen per sub-level (the
+//          "variant": throughput of one thread per edge on big frontiers,
+//          latency of a whole warp per edge on small ones);
+//   heavy  longer rows, cut into chunks of hc entries.  Appending a heavy
+//          edge reserves its chunk range with one 64-bit atomic on
+//          (edge count << 32 | chunk total), so the chunk bases are monotone
+//          in list order and any warp can map chunk index -> edge by binary
+//          search.  All warps of the grid share all chunks, so the few huge
+//          rows of a small late frontier spread over the whole GPU.
 //
 // Loop forms: PLAIN launches Scan / ProcessSubLevel from the host and reads
 // the frontier size back after every phase (the direct transcription of
@@ -37,28 +42,38 @@
 namespace {
 
 enum {
-    C_CNT = 0,   // [0..3] frontier size produced by phase p, slot p & 3
-    C_MIN = 4,   // [4..7] minimum live support above l found by phase p, slot p & 3
-    C_BAR_COUNT = 8,
-    C_BAR_GEN = 9,
-    C_ERR = 10,
-    C_NSUB = 11,
-    C_NSCAN = 12,
-    C_NLEVEL = 13,
-    C_LAST_L = 14,
-    C_TRI_LO = 16,  // triangle count (int64 at 16..17)
+    C_NL = 0,    // [0..3]   light-list size produced by phase p, slot p & 3
+    C_MIN = 4,   // [4..7]   minimum live support above l found by phase p
+    C_HC = 8,    // [8..15]  u64 per slot: heavy count << 32 | chunk total
+    C_BAR_COUNT = 16,
+    C_BAR_GEN = 17,
+    C_ERR = 18,
+    C_NSUB = 19,
+    C_NSCAN = 20,
+    C_NLEVEL = 21,
+    C_LAST_L = 22,
+    C_TRI = 24,  // [24..25] triangle count (u64), [26] max support
     C_TOTAL = 32
 };
 
-constexpr int PT = 256;              // threads per block in the peel kernels
-constexpr int APPEND_CAP = 2048;     // per-block staging for next-frontier appends
+constexpr int PT = 256;      // threads per block in the peel kernels
+constexpr int LIGHT = 32;    // shorter row <= LIGHT entries: light edge
+constexpr int LCAP = 1024;   // per-block staging of light next-frontier appends
+constexpr int HCAP = PT;     // per-block staging of heavy appends (one per thread at flush)
+
+// One side of the frontier ping-pong.
+struct Frontier {
+    int32_t* light;
+    int32_t* heavy;
+    uint32_t* cbase;  // first chunk number of each heavy edge (monotone)
+};
 
 struct PeelSmem {
-    int32_t buf[APPEND_CAP];
-    int bufcnt;
-    int qcnt;
-    int base;
-    int32_t q[PT][3];  // block-path queue: e1, shorter endpoint a, other b
+    int32_t lbuf[LCAP];
+    int32_t hbuf[HCAP];
+    int lcnt, hcnt, lbase, hq0;
+    uint32_t hb0;
+    uint32_t wsum[PT / 32];
 };
 
 template <typename Off>
@@ -67,34 +82,83 @@ struct Graph {
     const int32_t* __restrict__ col;
     const int32_t* __restrict__ eid;
     const int2* __restrict__ el;
+    const int32_t* __restrict__ dmin;  // min(d(u), d(v)) per edge
     int2* ss;
     int64_t m;
+    int hc;  // heavy chunk length (entries of the shorter row)
 };
 
-// Block-staged append to the next frontier: shared-memory slot first, the
-// global list directly when the staging buffer is full.
+__device__ __forceinline__ uint32_t nchunks_of(int d, int hc) { return (uint32_t)((d + hc - 1) / hc); }
+
+// Next-frontier append, staged per block in shared memory; a full stage
+// spills straight to the global lists.
 struct Appender {
     PeelSmem* sm;
-    int32_t* out;
-    int* count;
+    Frontier out;
+    int* nl;
+    unsigned long long* hcp;  // packed heavy counter
+    const int32_t* dmin;
+    int hc;
     __device__ __forceinline__ void push(int32_t f) const {
-        int p = atomicAdd(&sm->bufcnt, 1);
-        if (p < APPEND_CAP) {
-            sm->buf[p] = f;
+        const int d = __ldg(dmin + f);
+        if (d <= LIGHT) {
+            const int p = atomicAdd(&sm->lcnt, 1);
+            if (p < LCAP) {
+                sm->lbuf[p] = f;
+            } else {
+                out.light[atomicAdd(nl, 1)] = f;
+            }
         } else {
-            int q = atomicAdd(count, 1);
-            out[q] = f;
+            const int p = atomicAdd(&sm->hcnt, 1);
+            if (p < HCAP) {
+                sm->hbuf[p] = f;
+            } else {
+                const unsigned long long old = atomicAdd(hcp, (1ull << 32) | nchunks_of(d, hc));
+                const int q = (int)(old >> 32);
+                out.heavy[q] = f;
+                out.cbase[q] = (uint32_t)old;
+            }
         }
     }
-    // whole block; ends with the buffer empty
-    __device__ __forceinline__ void flush() const {
+    // whole block; leaves the stage empty
+    __device__ void flush() const {
         __syncthreads();
-        int k = min(sm->bufcnt, APPEND_CAP);
-        if (threadIdx.x == 0) sm->base = k ? atomicAdd(count, k) : 0;
+        const int kl = min(sm->lcnt, LCAP), kh = min(sm->hcnt, HCAP);
+        const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+        // exclusive scan of the staged heavy edges' chunk counts
+        const uint32_t c = t < kh ? nchunks_of(__ldg(dmin + sm->hbuf[t]), hc) : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm->wsum[warp] = x;
         __syncthreads();
-        for (int i = threadIdx.x; i < k; i += blockDim.x) out[sm->base + i] = sm->buf[i];
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < PT / 32; w++) {
+            if (w < warp) before += sm->wsum[w];
+            total += sm->wsum[w];
+        }
+        if (t == 0) {
+            sm->lbase = kl ? atomicAdd(nl, kl) : 0;
+            if (kh) {
+                const unsigned long long old = atomicAdd(hcp, ((unsigned long long)kh << 32) | total);
+                sm->hq0 = (int)(old >> 32);
+                sm->hb0 = (uint32_t)old;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) sm->bufcnt = 0;
+        for (int i = t; i < kl; i += blockDim.x) out.light[sm->lbase + i] = sm->lbuf[i];
+        if (t < kh) {
+            out.heavy[sm->hq0 + t] = sm->hbuf[t];
+            out.cbase[sm->hq0 + t] = sm->hb0 + before + x - c;
+        }
+        __syncthreads();
+        if (t == 0) {
+            sm->lcnt = 0;
+            sm->hcnt = 0;
+        }
         __syncthreads();
     }
 };
@@ -120,8 +184,22 @@ __device__ __forceinline__ void on_triangle(int2* ss, int32_t e1, int32_t x, int
     if (sy.x > l && (!inx || e1 < x)) relax(ss, y, l, g, ap);
 }
 
-// All triangles through e1 whose apex comes from slots j = start, start+step,
-// ... of the shorter row [a0, a1), probed in the longer row [b0, b1).
+template <typename Off>
+struct Rows {
+    Off a0, a1, b0, b1;  // shorter row [a0, a1), longer row [b0, b1)
+};
+
+template <typename Off>
+__device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
+    const int2 uv = __ldg(G.el + e);
+    const Off u0 = __ldg(G.rowptr + uv.x), u1 = __ldg(G.rowptr + uv.x + 1);
+    const Off v0 = __ldg(G.rowptr + uv.y), v1 = __ldg(G.rowptr + uv.y + 1);
+    if (u1 - u0 <= v1 - v0) return Rows<Off>{u0, u1, v0, v1};
+    return Rows<Off>{v0, v1, u0, u1};
+}
+
+// All triangles through e1 whose apex is one of the slots start, start+step,
+// ... of [a0, a1) (part of the shorter row), probed in the longer row [b0, b1).
 template <typename Off>
 __device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a0, Off a1, Off b0, Off b1, int start,
                                           int step, int32_t l, int32_t g, const Appender& ap) {
@@ -132,69 +210,90 @@ __device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a
     }
 }
 
-// One frontier, all blocks of the grid.  Blocks take tiles of PT frontier
-// edges in turn; inside a tile each edge goes to the thread, warp or block
-// path.  The per-block trip count is uniform, so __syncthreads is safe.
+// Largest q in [0, nh) with cb[q] <= w (cb ascending, cb[0] = 0).
+__device__ __forceinline__ int chunk_owner(const uint32_t* cb, int nh, uint32_t w) {
+    int lo = 0, hi = nh - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldcg(cb + mid) <= w) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One sub-level over the whole grid (ProcessSubLevel).  gsz = lanes per
+// light edge (1, 8 or 32); heavy chunks go one per warp.
 template <typename Off>
-__device__ void process_frontier(const Graph<Off>& G, const int32_t* curr, int ncurr, int32_t l, int32_t g,
-                                 int32_t* next, int* next_count, int variant, int thr_thread, int thr_block,
-                                 PeelSmem* sm) {
+__device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl, int nh, uint32_t nchunk, int gsz,
+                                 int32_t l, int32_t g, const Appender& ap) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    {
+        const int64_t ngrp = nth / gsz;
+        const int sub = (int)(gtid % gsz);
+        for (int64_t i = gtid / gsz; i < nl; i += ngrp) {
+            const int32_t e1 = __ldcg(cur.light + i);
+            const Rows<Off> r = rows_of<Off>(G, e1);
+            walk_rows<Off>(G, e1, r.a0, r.a1, r.b0, r.b1, sub, gsz, l, g, ap);
+        }
+    }
     const int lane = threadIdx.x & 31;
-    const Appender ap{sm, next, next_count};
-    const int ntiles = (ncurr + PT - 1) / PT;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int i = t * PT + threadIdx.x;
-        int cls = -1;
-        int32_t e1 = 0, a = 0, b = 0;
-        Off a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-        if (i < ncurr) {
-            e1 = __ldcg(curr + i);
-            int2 uv = __ldg(G.el + e1);
-            Off u0 = __ldg(G.rowptr + uv.x), u1 = __ldg(G.rowptr + uv.x + 1);
-            Off v0 = __ldg(G.rowptr + uv.y), v1 = __ldg(G.rowptr + uv.y + 1);
-            if (u1 - u0 <= v1 - v0) {
-                a = uv.x; b = uv.y; a0 = u0; a1 = u1; b0 = v0; b1 = v1;
-            } else {
-                a = uv.y; b = uv.x; a0 = v0; a1 = v1; b0 = u0; b1 = u1;
-            }
-            const int64_t da = (int64_t)(a1 - a0);
-            cls = variant >= 0 ? variant : (da <= thr_thread ? 0 : (da <= thr_block ? 1 : 2));
-        }
-        // thread path
-        if (cls == 0) walk_rows<Off>(G, e1, a0, a1, b0, b1, 0, 1, l, g, ap);
-        // warp path: the warp serves its warp-class lanes one after another
-        unsigned wm = __ballot_sync(FULL_MASK, cls == 1);
-        while (wm) {
-            const int src = __ffs(wm) - 1;
-            wm &= wm - 1;
-            int32_t e = __shfl_sync(FULL_MASK, e1, src);
-            Off x0 = __shfl_sync(FULL_MASK, a0, src), x1 = __shfl_sync(FULL_MASK, a1, src);
-            Off y0 = __shfl_sync(FULL_MASK, b0, src), y1 = __shfl_sync(FULL_MASK, b1, src);
-            walk_rows<Off>(G, e, x0, x1, y0, y1, lane, 32, l, g, ap);
-        }
-        // block path: queue, then the whole block per queued edge
-        if (cls == 2) {
-            int p = atomicAdd(&sm->qcnt, 1);
-            sm->q[p][0] = e1;
-            sm->q[p][1] = a;
-            sm->q[p][2] = b;
-        }
-        __syncthreads();
-        const int nq = sm->qcnt;
-        for (int k = 0; k < nq; k++) {
-            const int32_t e = sm->q[k][0], x = sm->q[k][1], y = sm->q[k][2];
-            walk_rows<Off>(G, e, __ldg(G.rowptr + x), __ldg(G.rowptr + x + 1), __ldg(G.rowptr + y),
-                           __ldg(G.rowptr + y + 1), threadIdx.x, PT, l, g, ap);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sm->qcnt = 0;
-        ap.flush();
+    const int64_t nw = nth / 32;
+    for (int64_t w = gtid / 32; w < (int64_t)nchunk; w += nw) {
+        const int q = chunk_owner(cur.cbase, nh, (uint32_t)w);
+        const int32_t e1 = __ldcg(cur.heavy + q);
+        const Rows<Off> r = rows_of<Off>(G, e1);
+        const int64_t s0 = (int64_t)r.a0 + (w - (int64_t)__ldcg(cur.cbase + q)) * G.hc;
+        const int64_t s1 = min((int64_t)r.a1, s0 + G.hc);
+        walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r.b0, r.b1, lane, 32, l, g, ap);
     }
 }
 
-// Scan at level l: curr <- {e : S[e] = l}, their stamps <- g; *minslot <-
-// min(*minslot, min{S[e] : S[e] > l}).  Two edges per 16-byte load.
-__device__ void scan_level(int2* ss, int64_t m, int32_t l, int32_t g, int32_t* curr, int* count, int* minslot) {
+// Lanes per light edge for a sub-level: a whole warp per edge while that
+// still leaves most of the grid's warps busy, 8 lanes while there are a
+// few edges per group, one thread per edge on big frontiers.
+__host__ __device__ __forceinline__ int pick_group(int variant, int64_t nl, int64_t nthreads) {
+    if (variant == TRUSS_VAR_THREAD) return 1;
+    if (variant == TRUSS_VAR_GROUP) return 8;
+    if (variant == TRUSS_VAR_WARP) return 32;
+    if (nl * 32 <= nthreads) return 32;
+    if (nl * 8 <= 4 * nthreads) return 8;
+    return 1;
+}
+
+// Warp-aggregated append of matched edges to the light or heavy list.
+__device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const int32_t* dmin, int hc,
+                                                     const Frontier& out, int* nl, unsigned long long* hcp) {
+    const int d = hit ? __ldg(dmin + e) : 0;
+    const bool light = hit && d <= LIGHT;
+    warp_append(light, e, out.light, nl);
+    const bool heavy = hit && !light;
+    const unsigned b = __ballot_sync(FULL_MASK, heavy);
+    if (b) {
+        const int lane = (int)lane_id();
+        const uint32_t c = heavy ? nchunks_of(d, hc) : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t total = __shfl_sync(FULL_MASK, x, 31);
+        unsigned long long old = 0;
+        if (lane == 0) old = atomicAdd(hcp, ((unsigned long long)__popc(b) << 32) | total);
+        old = __shfl_sync(FULL_MASK, old, 0);
+        if (heavy) {
+            const int q = (int)(old >> 32) + __popc(b & lanemask_lt());
+            out.heavy[q] = e;
+            out.cbase[q] = (uint32_t)old + x - c;
+        }
+    }
+}
+
+// Scan at level l: curr <- {e : S[e] = l} split into light / heavy lists,
+// their stamps <- g; *minslot <- min(*minslot, min{S[e] : S[e] > l}).  Two
+// edges per 16-byte load.
+__device__ void scan_level(int2* ss, int64_t m, int32_t l, int32_t g, const Frontier out, int* nl,
+                           unsigned long long* hcp, int* minslot, const int32_t* dmin, int hc) {
     const int64_t npair = (m + 1) / 2;
     const int4* ss4 = reinterpret_cast<const int4*>(ss);
     int mn = INT_MAX;
@@ -216,39 +315,56 @@ __device__ void scan_level(int2* ss, int64_t m, int32_t l, int32_t g, int32_t* c
         if (h1) ss[2 * p + 1].y = g;
         if (s0 > l) mn = min(mn, s0);
         if (s1 > l) mn = min(mn, s1);
-        warp_append(h0, (int32_t)(2 * p), curr, count);
-        warp_append(h1, (int32_t)(2 * p + 1), curr, count);
+        warp_classify_append(h0, (int32_t)(2 * p), dmin, hc, out, nl, hcp);
+        warp_classify_append(h1, (int32_t)(2 * p + 1), dmin, hc, out, nl, hcp);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
     if (lane_id() == 0 && mn != INT_MAX) atomicMin(minslot, mn);
 }
 
-// ------------------------------------------------------- standalone kernels
-
-__global__ void __launch_bounds__(PT) k_scan(int2* ss, int64_t m, int32_t l, int32_t g, int32_t* curr, int* count,
-                                              int* minslot) {
-    scan_level(ss, m, l, g, curr, count, minslot);
+__device__ __forceinline__ unsigned long long* hc_slot(int* ctr, int s) {
+    return reinterpret_cast<unsigned long long*>(ctr + C_HC) + s;
 }
 
+// ------------------------------------------------------- standalone kernels
+
+__global__ void __launch_bounds__(PT) k_scan(int2* ss, int64_t m, int32_t l, int32_t g, Frontier out, int* ctr,
+                                              const int32_t* dmin, int hc) {
+    scan_level(ss, m, l, g, out, ctr + C_NL, hc_slot(ctr, 0), ctr + C_MIN, dmin, hc);
+}
+
+// split a given edge list into light / heavy lists (state-level entry point)
+__global__ void k_classify(const int32_t* __restrict__ edges, int64_t k, const int32_t* dmin, int hc, Frontier out,
+                           int* ctr) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < k; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool hit = i < k;
+        warp_classify_append(hit, hit ? edges[i] : 0, dmin, hc, out, ctr + C_NL, hc_slot(ctr, 0));
+    }
+}
+
+// one sub-level: lists of side `cur` with the counts given, next lists into
+// side `nxt` counted in slot 1
 template <typename Off>
-__global__ void __launch_bounds__(PT) k_process(Graph<Off> G, const int32_t* curr, int ncurr, int32_t l, int32_t g,
-                                                int32_t* next, int* next_count, int variant, int thr_thread,
-                                                int thr_block) {
+__global__ void __launch_bounds__(PT) k_process(Graph<Off> G, Frontier cur, int nl, int nh, uint32_t nchunk, int gsz,
+                                                int32_t l, int32_t g, Frontier nxt, int* ctr) {
     __shared__ PeelSmem sm;
     if (threadIdx.x == 0) {
-        sm.bufcnt = 0;
-        sm.qcnt = 0;
+        sm.lcnt = 0;
+        sm.hcnt = 0;
     }
     __syncthreads();
-    process_frontier<Off>(G, curr, ncurr, l, g, next, next_count, variant, thr_thread, thr_block, &sm);
+    const Appender ap{&sm, nxt, ctr + C_NL + 1, hc_slot(ctr, 1), G.dmin, G.hc};
+    process_frontier<Off>(G, cur, nl, nh, nchunk, gsz, l, g, ap);
+    ap.flush();
 }
 
 // ------------------------------------------------------------ grid barrier
 
-// Sense-free generation barrier over all blocks of a cooperative launch.
-// Every wait is bounded: past timeout_ns the block records TRUSS_ETIMEOUT
-// and returns false; a block that sees an error recorded also returns false.
+// Generation barrier over all blocks of a cooperative launch.  Every wait is
+// bounded: past timeout_ns the block records TRUSS_ETIMEOUT and returns
+// false; a block that sees an error recorded also returns false.
 __device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
@@ -282,60 +398,76 @@ __device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns) {
     return s_ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // The whole of Algorithm 4 in one cooperative launch.  Every thread follows
-// the same (l, g, scan#) sequence because every branch depends only on
-// counters read after a barrier.
+// the same (l, g, phase) sequence because every branch depends only on
+// counters read after a barrier.  Phase p (each Scan and each sub-level)
+// writes its counters to slot p & 3; slot (p+2) & 3 is cleared during phase
+// p: its last readers read it right after the barrier that ended phase p-2,
+// and the barrier ending phase p-1 lies in between.
 template <typename Off>
 __global__ void __launch_bounds__(PT)
-    k_persistent(Graph<Off> G, int32_t* fr0, int32_t* fr1, int* ctr, int variant, int thr_thread, int thr_block,
-                 int level_jump, uint64_t timeout_ns, int32_t* rec_level, int64_t* rec_size, int64_t max_rec) {
+    k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int* ctr, int variant, int level_jump, uint64_t timeout_ns,
+                 int32_t* rec_level, int64_t* rec_size, int64_t max_rec) {
     __shared__ PeelSmem sm;
     if (threadIdx.x == 0) {
-        sm.bufcnt = 0;
-        sm.qcnt = 0;
+        sm.lcnt = 0;
+        sm.hcnt = 0;
     }
     __syncthreads();
     const unsigned nblocks = gridDim.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-    // Phase p (every Scan and every sub-level is one phase) writes its
-    // counters to slot p & 3.  Slot (p+2) & 3 is cleared during phase p: its
-    // last readers read it right after the barrier that ended phase p-2, and
-    // the barrier ending phase p-1 lies in between.
     int32_t l = 0, g = 0;
     int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0, p = 0;
+    auto clear_slot = [&](int64_t q) {
+        const int s = (int)(q & 3);
+        ctr[C_NL + s] = 0;
+        ctr[C_MIN + s] = INT_MAX;
+        *hc_slot(ctr, s) = 0ull;
+    };
     while (processed < G.m) {
-        if (leader) {
-            ctr[C_CNT + ((p + 2) & 3)] = 0;
-            ctr[C_MIN + ((p + 2) & 3)] = INT_MAX;
-        }
-        int32_t* curr = (g & 1) ? fr1 : fr0;
-        scan_level(G.ss, G.m, l, g, curr, ctr + C_CNT + (p & 3), ctr + C_MIN + (p & 3));
+        if (leader) clear_slot(p + 2);
+        const Frontier cur = (g & 1) ? f1 : f0;
+        const int s = (int)(p & 3);
+        scan_level(G.ss, G.m, l, g, cur, ctr + C_NL + s, hc_slot(ctr, s), ctr + C_MIN + s, G.dmin, G.hc);
         if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-        int c = ld_acquire_gpu(ctr + C_CNT + (p & 3));
-        const int mn = ld_acquire_gpu(ctr + C_MIN + (p & 3));
+        int nl = ld_acquire_gpu(ctr + C_NL + s);
+        unsigned long long hcv = ld_acquire_u64(hc_slot(ctr, s));
+        const int mn = ld_acquire_gpu(ctr + C_MIN + s);
         p++;
         sc++;
-        if (c == 0) {
+        if (nl + (int)(hcv >> 32) == 0) {
             if (mn == INT_MAX) break;
             l = level_jump ? mn : l + 1;
             continue;
         }
         nlevel++;
-        while (c > 0) {
-            processed += c;
+        while (nl + (int)(hcv >> 32) > 0) {
+            const int nh = (int)(hcv >> 32);
+            const uint32_t nchunk = (uint32_t)hcv;
+            processed += nl + nh;
+            const int q = (int)(p & 3);
             if (leader) {
                 if (nsub < max_rec) {
                     rec_level[nsub] = l;
-                    rec_size[nsub] = c;
+                    rec_size[nsub] = nl + nh;
                 }
-                ctr[C_CNT + ((p + 2) & 3)] = 0;
-                ctr[C_MIN + ((p + 2) & 3)] = INT_MAX;
+                clear_slot(p + 2);
             }
-            int32_t* cu = (g & 1) ? fr1 : fr0;
-            int32_t* nx = (g & 1) ? fr0 : fr1;
-            process_frontier<Off>(G, cu, c, l, g, nx, ctr + C_CNT + (p & 3), variant, thr_thread, thr_block, &sm);
+            const Frontier cu = (g & 1) ? f1 : f0;
+            const Frontier nx = (g & 1) ? f0 : f1;
+            const Appender ap{&sm, nx, ctr + C_NL + q, hc_slot(ctr, q), G.dmin, G.hc};
+            process_frontier<Off>(G, cu, nl, nh, nchunk, pick_group(variant, nl, nthreads), l, g, ap);
+            ap.flush();
             if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-            c = ld_acquire_gpu(ctr + C_CNT + (p & 3));
+            nl = ld_acquire_gpu(ctr + C_NL + q);
+            hcv = ld_acquire_u64(hc_slot(ctr, q));
             p++;
             g++;
             nsub++;
@@ -356,6 +488,12 @@ __global__ void k_truss_out(const int2* __restrict__ ss, int64_t m, const int32_
                             int32_t* __restrict__ out, int add) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
         out[perm ? perm[e] : e] = ss[e].x + add;
+}
+
+__global__ void k_step_out(const int2* __restrict__ ss, int64_t m, const int32_t* __restrict__ perm,
+                           int32_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[perm ? perm[e] : e] = ss[e].y;
 }
 
 __global__ void k_sum_support(const int2* __restrict__ ss, int64_t m, unsigned long long* out, int* smax) {
@@ -418,9 +556,16 @@ __global__ void k_map_ids(const int32_t* __restrict__ in, int64_t k, const int32
         out[i] = map ? map[in[i]] : in[i];
 }
 
-// heuristic split of frontier edges by the length of the shorter row
-constexpr int THR_THREAD = 8;
-constexpr int THR_BLOCK = 2048;
+template <typename Off>
+__global__ void k_dmin(const Off* __restrict__ rowptr, const int2* __restrict__ el, int64_t m, int32_t* __restrict__ dmin) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        int2 xy = el[e];
+        int64_t du = (int64_t)(rowptr[xy.x + 1] - rowptr[xy.x]), dv = (int64_t)(rowptr[xy.y + 1] - rowptr[xy.y]);
+        dmin[e] = (int32_t)min(du, dv);
+    }
+}
+
+// ------------------------------------------------------------- host side
 
 template <typename Off>
 int process_blocks(const truss_graph* g) {
@@ -431,7 +576,11 @@ int process_blocks(const truss_graph* g) {
 
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
-    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->ss, g->m};
+    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, g->ss, g->m, g->hc};
+}
+
+Frontier side(truss_graph* g, int k) {
+    return Frontier{g->fq[k][0], g->fq[k][1], reinterpret_cast<uint32_t*>(g->fq[k][2])};
 }
 
 struct RunOut {
@@ -440,7 +589,7 @@ struct RunOut {
 };
 
 // Algorithm 4's loop driven from the host: one Scan launch per level, one
-// ProcessSubLevel launch per sub-level, the frontier size read back after each.
+// ProcessSubLevel launch per sub-level, the frontier sizes read back after each.
 template <typename Off>
 int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, std::vector<int32_t>* rl,
               std::vector<int64_t>* rs, RunOut* out) {
@@ -451,35 +600,48 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, std::vector<i
     const int pmax = process_blocks<Off>(g);
     int32_t l = 0, gs = 0;
     int64_t processed = 0;
+    auto read_slot = [&](int slot, int* nl, int* nh, uint32_t* nc) {
+        unsigned long long v;
+        memcpy(&v, h + C_HC + 2 * slot, sizeof(v));
+        *nl = h[C_NL + slot];
+        *nh = (int)(v >> 32);
+        *nc = (uint32_t)v;
+    };
     while (processed < g->m) {
-        // counters: [0] curr size, [4] min above
         k_init_counters<<<1, 32, 0, s>>>(ctr);
-        k_scan<<<sblocks, PT, 0, s>>>(g->ss, g->m, l, gs, g->fr[gs & 1], ctr + C_CNT, ctr + C_MIN);
+        k_scan<<<sblocks, PT, 0, s>>>(g->ss, g->m, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc);
         CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(h, ctr, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+        truss_note_launch(2);
+        CU(cudaMemcpyAsync(h, ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         out->nscan++;
-        int c = h[C_CNT];
-        if (c == 0) {
+        int nl, nh;
+        uint32_t nc;
+        read_slot(0, &nl, &nh, &nc);
+        if (nl + nh == 0) {
             if (h[C_MIN] == INT_MAX) break;
             l = o.level_jump ? h[C_MIN] : l + 1;
             continue;
         }
         out->nlevel++;
-        while (c > 0) {
-            processed += c;
+        while (nl + nh > 0) {
+            processed += nl + nh;
             if (rl) {
                 rl->push_back(l);
-                rs->push_back(c);
+                rs->push_back(nl + nh);
             }
-            CU(cudaMemsetAsync(ctr + C_CNT + 1, 0, sizeof(int), s));
-            const int blocks = std::min(pmax, (c + PT - 1) / PT);
-            k_process<Off><<<blocks, PT, 0, s>>>(G, g->fr[gs & 1], c, l, gs, g->fr[(gs + 1) & 1], ctr + C_CNT + 1,
-                                                 o.variant, THR_THREAD, THR_BLOCK);
+            // next lists are counted in slot 1
+            CU(cudaMemsetAsync(ctr + C_NL + 1, 0, sizeof(int), s));
+            CU(cudaMemsetAsync(ctr + C_HC + 2, 0, sizeof(unsigned long long), s));
+            const int gmax = pick_group(o.variant, nl, (int64_t)pmax * PT);
+            const int64_t want = std::max<int64_t>(((int64_t)nl * gmax + PT - 1) / PT, ((int64_t)nc * 32 + PT - 1) / PT);
+            const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(pmax, want));
+            k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, gs & 1), nl, nh, nc, gmax, l, gs, side(g, (gs + 1) & 1), ctr);
             CU(cudaGetLastError());
-            CU(cudaMemcpyAsync(h + 1, ctr + C_CNT + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            truss_note_launch();
+            CU(cudaMemcpyAsync(h, ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
-            c = h[1];
+            read_slot(1, &nl, &nh, &nc);
             gs++;
             out->nsub++;
         }
@@ -499,19 +661,19 @@ int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, int32_t*
     k_init_counters<<<1, 32, 0, s>>>(g->ctr);
     CU(cudaGetLastError());
     int variant = o.variant;
-    int thr_t = THR_THREAD, thr_b = THR_BLOCK, jump = o.level_jump;
+    int jump = o.level_jump;
     uint64_t tmo = o.timeout_ns > 0 ? (uint64_t)o.timeout_ns : 10000000000ull;
-    int32_t* fr0 = g->fr[0];
-    int32_t* fr1 = g->fr[1];
+    Frontier f0 = side(g, 0), f1 = side(g, 1);
     int* ctr = g->ctr;
-    void* args[] = {&G, &fr0, &fr1, &ctr, &variant, &thr_t, &thr_b, &jump, &tmo, &d_rl, &d_rs, &max_rec};
+    void* args[] = {&G, &f0, &f1, &ctr, &variant, &jump, &tmo, &d_rl, &d_rs, &max_rec};
     CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off>, dim3(blocks), dim3(PT), args, 0, s));
+    truss_note_launch(2);
     return TRUSS_OK;
 }
 
 int check_opts(const truss_opts& o) {
     if (o.loop != TRUSS_LOOP_PLAIN && o.loop != TRUSS_LOOP_PERSISTENT) return TRUSS_EINVAL;
-    if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_BLOCK) return TRUSS_EINVAL;
+    if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_WARP) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size || o.max_sub < 0 || !o.sync))
         return TRUSS_EINVAL;
     return TRUSS_OK;
@@ -520,26 +682,29 @@ int check_opts(const truss_opts& o) {
 template <typename Off>
 int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_stats* st, cudaStream_t s) {
     TRY(truss_ensure_workspace(g));
+    const long long launches0 = truss_launch_count();
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     const bool timed = o.sync && st;
     if (timed)
         for (auto& e : ev) CU(cudaEventCreate(&e));
     if (timed) CU(cudaEventRecord(ev[0], s));
     TRY(truss_support_internal(g, g->ss, s));
-    unsigned long long* d_tri = reinterpret_cast<unsigned long long*>(g->ctr + C_TRI_LO);
+    unsigned long long* d_tri = reinterpret_cast<unsigned long long*>(g->ctr + C_TRI);
     if (st) {
-        CU(cudaMemsetAsync(g->ctr + C_TRI_LO, 0, 4 * sizeof(int), s));
-        k_sum_support<<<grid_for(g->m, 256, (int64_t)g->sms * 4), 256, 0, s>>>(g->ss, g->m, d_tri, g->ctr + C_TRI_LO + 2);
+        CU(cudaMemsetAsync(g->ctr + C_TRI, 0, 4 * sizeof(int), s));
+        k_sum_support<<<grid_for(g->m, 256, (int64_t)g->sms * 4), 256, 0, s>>>(g->ss, g->m, d_tri, g->ctr + C_TRI + 2);
         CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(g->h_ctr + C_TRI_LO, g->ctr + C_TRI_LO, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        truss_note_launch();
+        CU(cudaMemcpyAsync(g->h_ctr + C_TRI, g->ctr + C_TRI, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     }
     if (timed) CU(cudaEventRecord(ev[1], s));
     RunOut ro;
     std::vector<int32_t> rl;
     std::vector<int64_t> rs;
     const bool rec = o.h_sub_level && o.max_sub > 0;
+    int rc = TRUSS_OK;
     if (o.loop == TRUSS_LOOP_PLAIN) {
-        TRY(run_plain<Off>(g, o, s, rec ? &rl : nullptr, rec ? &rs : nullptr, &ro));
+        rc = run_plain<Off>(g, o, s, rec ? &rl : nullptr, rec ? &rs : nullptr, &ro);
     } else {
         int32_t* d_rl = nullptr;
         int64_t* d_rs = nullptr;
@@ -547,9 +712,9 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             CU(cudaMallocAsync((void**)&d_rl, sizeof(int32_t) * (size_t)o.max_sub, s));
             CU(cudaMallocAsync((void**)&d_rs, sizeof(int64_t) * (size_t)o.max_sub, s));
         }
-        int rc = run_persistent<Off>(g, o, s, d_rl, d_rs, rec ? o.max_sub : 0);
+        rc = run_persistent<Off>(g, o, s, d_rl, d_rs, rec ? o.max_sub : 0);
         if (rc == TRUSS_OK && o.sync) {
-            CU(cudaMemcpyAsync(g->h_ctr, g->ctr, sizeof(int) * C_TRI_LO, cudaMemcpyDeviceToHost, s));
+            CU(cudaMemcpyAsync(g->h_ctr, g->ctr, sizeof(int) * C_TRI, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             if (g->h_ctr[C_ERR]) rc = g->h_ctr[C_ERR];
             ro.nsub = g->h_ctr[C_NSUB];
@@ -564,14 +729,21 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         }
         if (d_rl) cudaFreeAsync(d_rl, s);
         if (d_rs) cudaFreeAsync(d_rs, s);
-        if (rc != TRUSS_OK) {
-            if (timed)
-                for (auto& e : ev) cudaEventDestroy(e);
-            return rc;
-        }
+    }
+    if (rc != TRUSS_OK) {
+        if (timed)
+            for (auto& e : ev) cudaEventDestroy(e);
+        return rc;
     }
     if (timed) CU(cudaEventRecord(ev[2], s));
-    if (g->m > 0) k_truss_out<<<grid_for(g->m, 256), 256, 0, s>>>(g->ss, g->m, g->perm, d_truss, 2);
+    if (g->m > 0) {
+        k_truss_out<<<grid_for(g->m, 256), 256, 0, s>>>(g->ss, g->m, g->perm, d_truss, 2);
+        truss_note_launch();
+        if (o.d_peel_step) {
+            k_step_out<<<grid_for(g->m, 256), 256, 0, s>>>(g->ss, g->m, g->perm, o.d_peel_step);
+            truss_note_launch();
+        }
+    }
     CU(cudaGetLastError());
     if (o.sync) {
         CU(cudaStreamSynchronize(s));
@@ -587,11 +759,14 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         st->sublevels = ro.nsub;
         st->scans = ro.nscan;
         st->levels = (int32_t)ro.nlevel;
+        st->launches = truss_launch_count() - launches0;
+        st->wedges_up = g->wedges_up;
+        st->dmin_sum = g->dmin_sum;
         if (o.sync) {
             unsigned long long tri = 0;
-            memcpy(&tri, g->h_ctr + C_TRI_LO, sizeof(tri));
+            memcpy(&tri, g->h_ctr + C_TRI, sizeof(tri));
             st->triangles = (int64_t)(tri / 3);
-            // largest level that held edges: the last l before the loop ended
+            // the last level that held edges is the final l minus one
             st->t_max = g->m > 0 ? ro.last_l - 1 + 2 : 0;
         }
         if (timed) {
@@ -609,34 +784,46 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
                        int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant, cudaStream_t s) {
     TRY(truss_ensure_workspace(g));
     const int64_t m = g->m;
-    int32_t* inv = nullptr;
+    int32_t *inv = nullptr, *cur = nullptr;
+    CU(cudaMallocAsync((void**)&cur, sizeof(int32_t) * (size_t)(ncurr > 0 ? ncurr : 1), s));
     if (g->perm) {
         CU(cudaMallocAsync((void**)&inv, sizeof(int32_t) * (size_t)m, s));
         k_inverse_perm<<<grid_for(m, 256), 256, 0, s>>>(g->perm, m, inv);
     }
     k_import_state<<<grid_for(m, 256), 256, 0, s>>>(d_S, d_flags, g->perm, m, g->ss);
+    k_init_counters<<<1, 32, 0, s>>>(g->ctr);
     if (ncurr > 0) {
-        k_map_ids<<<grid_for(ncurr, 256), 256, 0, s>>>(d_curr, ncurr, inv, g->fr[0]);
-        k_mark_curr<<<grid_for(ncurr, 256), 256, 0, s>>>(g->fr[0], ncurr, g->ss);
+        k_map_ids<<<grid_for(ncurr, 256), 256, 0, s>>>(d_curr, ncurr, inv, cur);
+        k_mark_curr<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->ss);
+        k_classify<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->dmin, g->hc, side(g, 0), g->ctr);
     }
-    CU(cudaMemsetAsync(g->ctr, 0, sizeof(int) * 2, s));
     CU(cudaGetLastError());
-    if (ncurr > 0) {
+    int* h = g->h_ctr;
+    CU(cudaMemcpyAsync(h, g->ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    unsigned long long v;
+    memcpy(&v, h + C_HC, sizeof(v));
+    const int nl = h[C_NL], nh = (int)(v >> 32);
+    const uint32_t nc = (uint32_t)v;
+    if (nl + nh > 0) {
         Graph<Off> G = graph_view<Off>(g);
-        const int blocks = std::min<int64_t>(process_blocks<Off>(g), (ncurr + PT - 1) / PT);
-        k_process<Off><<<blocks, PT, 0, s>>>(G, g->fr[0], (int)ncurr, l, 1, g->fr[1], g->ctr + 1, variant, THR_THREAD,
-                                             THR_BLOCK);
+        const int blocks = process_blocks<Off>(g);
+        k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, 0), nl, nh, nc, pick_group(variant, nl, (int64_t)blocks * PT), l,
+                                             1, side(g, 1), g->ctr);
         CU(cudaGetLastError());
     }
-    int nn = 0;
-    CU(cudaMemcpyAsync(&nn, g->ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h, g->ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (nn > 0) k_map_ids<<<grid_for(nn, 256), 256, 0, s>>>(g->fr[1], nn, g->perm, d_next);
+    memcpy(&v, h + C_HC + 2, sizeof(v));
+    const int nl1 = h[C_NL + 1], nh1 = (int)(v >> 32);
+    if (nl1 > 0) k_map_ids<<<grid_for(nl1, 256), 256, 0, s>>>(g->fq[1][0], nl1, g->perm, d_next);
+    if (nh1 > 0) k_map_ids<<<grid_for(nh1, 256), 256, 0, s>>>(g->fq[1][1], nh1, g->perm, d_next + nl1);
     k_export_state<<<grid_for(m, 256), 256, 0, s>>>(g->ss, g->perm, m, d_S, d_flags);
     CU(cudaGetLastError());
     if (inv) cudaFreeAsync(inv, s);
+    cudaFreeAsync(cur, s);
     CU(cudaStreamSynchronize(s));
-    *h_nnext = nn;
+    *h_nnext = nl1 + nh1;
     return TRUSS_OK;
 }
 
@@ -645,22 +832,40 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 int truss_ensure_workspace(truss_graph* g) {
     if (g->ctr) return TRUSS_OK;
     const size_t m = (size_t)(g->m > 0 ? g->m : 1);
+    // heavy chunk length: 64 entries, longer when the graph is so large that
+    // a sub-level's chunk total could leave 32 bits
+    int64_t hc = 64;
+    while ((int64_t)g->m + g->dmin_sum / hc >= ((int64_t)1 << 32) - 1) hc *= 2;
+    g->hc = (int)hc;
     CU(cudaMalloc((void**)&g->ss, sizeof(int2) * (m + 1)));
-    CU(cudaMalloc((void**)&g->fr[0], sizeof(int32_t) * m));
-    CU(cudaMalloc((void**)&g->fr[1], sizeof(int32_t) * m));
+    CU(cudaMalloc((void**)&g->dmin, sizeof(int32_t) * m));
+    for (int k = 0; k < 2; k++)
+        for (int j = 0; j < 3; j++) CU(cudaMalloc((void**)&g->fq[k][j], sizeof(int32_t) * m));
     CU(cudaMalloc((void**)&g->ctr, sizeof(int) * C_TOTAL));
     CU(cudaMallocHost((void**)&g->h_ctr, sizeof(int) * C_TOTAL));
+    if (g->m > 0) {
+        if (g->off64)
+            k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin);
+        else
+            k_dmin<int32_t><<<grid_for(g->m, 256), 256>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin);
+        CU(cudaGetLastError());
+        CU(cudaDeviceSynchronize());
+    }
     return TRUSS_OK;
 }
 
 void truss_release_workspace(truss_graph* g) {
     cudaFree(g->ss);
-    cudaFree(g->fr[0]);
-    cudaFree(g->fr[1]);
+    cudaFree(g->dmin);
+    for (int k = 0; k < 2; k++)
+        for (int j = 0; j < 3; j++) {
+            cudaFree(g->fq[k][j]);
+            g->fq[k][j] = nullptr;
+        }
     cudaFree(g->ctr);
     cudaFreeHost(g->h_ctr);
     g->ss = nullptr;
-    g->fr[0] = g->fr[1] = nullptr;
+    g->dmin = nullptr;
     g->ctr = nullptr;
     g->h_ctr = nullptr;
 }
@@ -701,9 +906,7 @@ extern "C" int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opt
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (g->m == 0) {
-        if (stats) {
-            memset(stats, 0, sizeof(*stats));
-        }
+        if (stats) memset(stats, 0, sizeof(*stats));
         return TRUSS_OK;
     }
     return g->off64 ? decompose_impl<int64_t>(g, d_truss, o, stats, s) : decompose_impl<int32_t>(g, d_truss, o, stats, s);
@@ -729,7 +932,7 @@ extern "C" int truss_sync(truss_graph* g, void* stream) {
 extern "C" int truss_peel_sublevel(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr,
                                    int64_t ncurr, int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant,
                                    void* stream) {
-    if (!g || !h_nnext || ncurr < 0 || ncurr > g->m || variant < TRUSS_VAR_AUTO || variant > TRUSS_VAR_BLOCK)
+    if (!g || !h_nnext || ncurr < 0 || ncurr > g->m || variant < TRUSS_VAR_AUTO || variant > TRUSS_VAR_WARP)
         return TRUSS_EINVAL;
     if (g->m > 0 && (!d_S || !d_flags || !d_next)) return TRUSS_EINVAL;
     if (ncurr > 0 && !d_curr) return TRUSS_EINVAL;

@@ -235,10 +235,12 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     int* S2 = (int*)ss;
     k_init_ss<<<grid_for(g->m, 256), 256, 0, s>>>(ss, g->m);
     CU(cudaGetLastError());
+    truss_note_launch();
     if (g->n > 0 && g->m > 0) {
         int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
         k_support_warp<Off><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
         CU(cudaGetLastError());
+        truss_note_launch();
     }
     if (g->n_sup_big > 0) {
         const int cap = TRUSS_SUP_BLOCK_CAP;
@@ -251,11 +253,13 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
         int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
         k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S2);
         CU(cudaGetLastError());
+        truss_note_launch();
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
         k_support_global<Off><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S2);
         CU(cudaGetLastError());
+        truss_note_launch();
     }
     return TRUSS_OK;
 }

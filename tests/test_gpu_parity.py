@@ -101,7 +101,7 @@ def test_edge_list_and_support(pkt, name, g, relabel, off64):
 # ------------------------------------------------------------ decomposition
 
 LOOPS = ["plain", "persistent"]
-VARIANTS = ["auto", "thread", "warp", "block"]
+VARIANTS = ["auto", "thread", "group", "warp"]
 
 
 def _loop(pkt, name):
@@ -109,7 +109,7 @@ def _loop(pkt, name):
 
 
 def _var(pkt, name):
-    return {"auto": pkt.VAR_AUTO, "thread": pkt.VAR_THREAD, "warp": pkt.VAR_WARP, "block": pkt.VAR_BLOCK}[name]
+    return {"auto": pkt.VAR_AUTO, "thread": pkt.VAR_THREAD, "group": pkt.VAR_GROUP, "warp": pkt.VAR_WARP}[name]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -189,7 +189,7 @@ def test_closed_forms(pkt):
     assert np.all(host(G.decompose()) == 2)
     G = pkt.build_csr(dev(np.zeros(n - 1)), dev(np.arange(1, n)), n)
     assert np.all(host(G.decompose()) == 2)
-    # wheel with a 3000-vertex rim: hub row long enough for the block path
+    # wheel with a 3000-vertex rim: hub rows long enough to be split
     k = 3000
     src = np.concatenate([np.zeros(k), np.arange(1, k + 1)])
     dst = np.concatenate([np.arange(1, k + 1), np.arange(1, k + 1) % k + 1])
@@ -316,3 +316,20 @@ def test_stats(pkt):
     assert st["m"] == eu.size
     _, lv, sz = oracle.pkt_serial(g.n, eu, ev)
     assert st["sublevels"] == sz.size and st["levels"] == np.unique(lv).size
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_peel_steps_match_serial_run_and_certify(pkt, loop):
+    """The sub-level each edge was peeled in equals the serial run's, and
+    the (trussness, peel step) pair passes the certificate."""
+    import torch
+
+    for name, g in SMALL:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+        step = torch.empty(G.m, dtype=torch.int32, device="cuda")
+        tau = host(G.decompose(loop=_loop(pkt, loop), peel_step=step))
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        want, _, _, ostep = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+        assert np.array_equal(tau, want), name
+        assert np.array_equal(host(step), ostep), name
+        assert oracle.certify(g.n, eu, ev, tau, host(step))[0] == 0

@@ -305,3 +305,36 @@ def test_batch_matches_single():
     for g, t in zip(gs, taus):
         eu, ev, tau = oracle.truss_of_edges(g.n, g.src, g.dst)
         assert np.array_equal(t, tau)
+
+
+# ------------------------------------------------------------ certificate
+
+def test_certificate_accepts_the_exact_answer():
+    for name, g in list(_invariant_graphs()) + [("rmat10", gg.workload("rmat10_ef8"))]:
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        tau, lv, sz, step = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+        bad, first = oracle.certify(g.n, eu, ev, tau, step, nthreads=4)
+        assert bad == 0 and first == -1, name
+
+
+def test_certificate_rejects_wrong_answers():
+    """Raising or lowering one edge's claim, or breaking the order, must be
+    caught (each pin of the certificate has a planted mistake here)."""
+    g = gg.rmat(9, 8, seed=3)
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    tau, lv, sz, step = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+    rng = np.random.default_rng(0)
+    tri = np.nonzero(tau > 2)[0]
+    for e in rng.choice(tri, 20, replace=False):
+        for d in (-1, 1):
+            t2 = tau.copy()
+            t2[e] += d
+            assert oracle.certify(g.n, eu, ev, t2, step)[0] > 0
+    # uniform shift of every claim
+    assert oracle.certify(g.n, eu, ev, tau + 1, step)[0] > 0
+    # an order that puts a high-trussness edge first
+    s2 = step.copy()
+    s2[np.argmax(tau)] = step.min()
+    assert oracle.certify(g.n, eu, ev, tau, s2)[0] > 0
+    # all claims 2 (a valid lower bound, but no valid order)
+    assert oracle.certify(g.n, eu, ev, np.full_like(tau, 2), step)[0] > 0
