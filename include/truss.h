@@ -52,6 +52,8 @@ extern "C" {
 #define TRUSS_EBADGRAPH (-6) /* a vertex id outside [0, n)                   */
 #define TRUSS_EDEVICE (-7)   /* a device-side consistency check failed       */
 #define TRUSS_ENOTSUP (-8)   /* the requested form is not available here     */
+#define TRUSS_ETOOBIG (-9)   /* input larger than a fixed-capacity entry
+                                point accepts                               */
 
 /* Human-readable text for a status.  Never NULL; static storage. */
 TRUSS_API const char* truss_strerror(int status);
@@ -226,6 +228,42 @@ TRUSS_API int truss_decompose_host(const int32_t* h_src, const int32_t* h_dst, i
 /* Wait for the graph's pending device work on `stream` and return any
  * latched device-side error (and clear it). */
 TRUSS_API int truss_sync(truss_graph* g, void* stream);
+
+/* ---------------------------------------------- allocation-free support */
+
+/* Largest vertex count truss_support_noalloc accepts. */
+#define TRUSS_NOALLOC_MAX_VERTICES (1 << 22)
+
+/*
+ * truss_support_noalloc -- per-edge triangle support S(e) (as truss_support)
+ * for a graph the caller already holds on the device, without allocating
+ * any device memory.  The paper has no counterpart: it exists for callers
+ * that must not call cudaMalloc or cudaFree -- e.g. a process whose
+ * framework allocator owns all device memory, or a latency-critical loop with
+ * a fixed memory budget.  Every other entry point allocates workspace.
+ *   d_rowptr : device int32[n+1], row offsets of the symmetric adjacency
+ *              (Es of Fig. 2), d_rowptr[n] = 2m.
+ *   d_col    : device int32[2m], neighbours, each row strictly ascending, no
+ *              self-loops (N of Fig. 2).
+ *   d_eid    : device int32[2m], the edge id in [0, m) of every slot; both
+ *              slots of an edge carry the same id (Eid of Fig. 2).
+ *   n, m     : vertices (0 <= n <= TRUSS_NOALLOC_MAX_VERTICES) and edges.
+ *   d_support: device int32[m], indexed by edge id (written).
+ * Scratch: a fixed array of (TRUSS_NOALLOC_MAX_VERTICES + 64) int32 (16 MiB)
+ * in the library's device memory, held by every GPU that loads the library
+ * until the process exits.  The first call on each device looks up that
+ * array's address (cudaGetSymbolAddress, with the device current) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * array, so calls whose device work overlaps (on two streams, or from two
+ * host threads) race and must be serialised by the caller.
+ * Synchronises `stream`.  Returns TRUSS_ETOOBIG when n exceeds the maximum,
+ * TRUSS_EBADGRAPH when the kernel met a neighbour or edge id out of range
+ * (those entries are skipped, never written through), TRUSS_EINVAL for null
+ * pointers or negative sizes.  Rows that are not sorted, or offsets outside
+ * [0, 2m], are not detected.
+ */
+TRUSS_API int truss_support_noalloc(const int32_t* d_rowptr, const int32_t* d_col, const int32_t* d_eid, int32_t n,
+                                    int64_t m, int32_t* d_support, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtruss.so")
 
 OK = 0
-EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP = -1, -2, -3, -4, -5, -6, -7, -8
+EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP, ETOOBIG = -1, -2, -3, -4, -5, -6, -7, -8, -9
+NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
 LOOP_PLAIN, LOOP_PERSISTENT = 0, 1
@@ -34,7 +35,7 @@ PROCESSED, IN_CURR = 1, 2
 EXPORTS = (
     "truss_strerror", "truss_build_csr", "truss_free", "truss_num_edges", "truss_num_vertices",
     "truss_edge_list", "truss_csr_copy", "truss_support", "truss_default_opts", "truss_decompose",
-    "truss_peel_sublevel", "truss_decompose_host", "truss_sync",
+    "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
 )
 
 
@@ -82,6 +83,7 @@ def _declare(lib):
     lib.truss_decompose_host.argtypes = [vp, vp, i64, i32, u32, vp, i64, ctypes.POINTER(i64),
                                          ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
     lib.truss_sync.argtypes = [vp, vp]
+    lib.truss_support_noalloc.argtypes = [vp, vp, vp, i32, i64, vp, vp]
     for name in EXPORTS:
         if name not in ("truss_strerror", "truss_free", "truss_default_opts"):
             getattr(lib, name).restype = ctypes.c_int

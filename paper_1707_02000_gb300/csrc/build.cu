@@ -40,6 +40,7 @@ extern "C" const char* truss_strerror(int status) {
         case TRUSS_EBADGRAPH: return "vertex id outside [0, n)";
         case TRUSS_EDEVICE: return "device-side consistency check failed";
         case TRUSS_ENOTSUP: return "not supported";
+        case TRUSS_ETOOBIG: return "input exceeds the fixed capacity of this entry point";
         default: return "unknown status";
     }
 }
