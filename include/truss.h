@@ -137,6 +137,21 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 #define TRUSS_VAR_GROUP 1     /* eight lanes per light edge                  */
 #define TRUSS_VAR_WARP 2      /* one warp per light edge                     */
 
+/* One record per non-empty sub-level (see truss_opts.h_trace). */
+typedef struct truss_sublevel_trace {
+    int32_t level;     /* support level l                                     */
+    int32_t group;     /* lanes per light edge used (1, 8 or 32)              */
+    int32_t n_light;   /* frontier edges with shorter row <= 32 entries       */
+    int32_t n_heavy;   /* the other frontier edges                            */
+    uint32_t n_chunks; /* heavy-row chunks shared out to warps                */
+    int32_t dmax;      /* longest shorter row in the frontier                 */
+    int64_t dsum;      /* sum of shorter-row lengths over the frontier        */
+    int64_t todo;      /* edges not yet peeled when the sub-level starts      */
+    int64_t t_ns;      /* device time of the sub-level, barrier to barrier    */
+    int64_t scan_ns;   /* device time of the Scans since the previous record
+                          (the Scan, or empty Scans, that opened this level) */
+} truss_sublevel_trace;
+
 typedef struct truss_opts {
     int32_t loop;        /* TRUSS_LOOP_*                                      */
     int32_t variant;     /* TRUSS_VAR_*                                       */
@@ -153,7 +168,9 @@ typedef struct truss_opts {
                              number of the sub-level (0, 1, ...) in which each
                              edge was peeled -- a peeling order that lets a
                              checker certify the result (see truss_decompose) */
-    int32_t reserved[6];
+    truss_sublevel_trace* h_trace; /* optional host array of max_sub records,
+                             one per sub-level; needs sync = 1               */
+    int32_t reserved[4];
 } truss_opts;
 
 typedef struct truss_stats {

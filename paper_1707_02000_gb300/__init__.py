@@ -50,7 +50,13 @@ class Opts(ctypes.Structure):
                 ("level_jump", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("h_sub_level", ctypes.POINTER(ctypes.c_int32)), ("h_sub_size", ctypes.POINTER(ctypes.c_int64)),
                 ("max_sub", ctypes.c_int64), ("d_peel_step", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("h_trace", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 4)]
+
+
+# truss_sublevel_trace, one record per sub-level
+TRACE_DTYPE = np.dtype([("level", "<i4"), ("group", "<i4"), ("n_light", "<i4"), ("n_heavy", "<i4"),
+                        ("n_chunks", "<u4"), ("dmax", "<i4"), ("dsum", "<i8"), ("todo", "<i8"), ("t_ns", "<i8"),
+                        ("scan_ns", "<i8")])
 
 
 class Stats(ctypes.Structure):
@@ -190,14 +196,20 @@ class Graph:
 
     def decompose(self, out=None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, sync=True, level_jump=True,
                   timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False,
-                  peel_step=None):
+                  peel_step=None, trace=False):
         """Trussness (int32[m], canonical order).  With ``record`` also
-        returns the (level, |curr|) of every sub-level; with ``stats`` a
-        dict of run statistics; ``peel_step`` (a CUDA int32[m] tensor)
-        receives the sub-level each edge was peeled in."""
+        returns the (level, |curr|) of every sub-level; with ``trace`` a
+        structured array (TRACE_DTYPE) with one record per sub-level; with
+        ``stats`` a dict of run statistics; ``peel_step`` (a CUDA int32[m]
+        tensor) receives the sub-level each edge was peeled in."""
         out = self._empty(self.m) if out is None else out
-        o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record)),
+        o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record or trace)),
                          level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
+        tr = None
+        if trace:
+            tr = np.zeros(max_sub, TRACE_DTYPE)
+            o.h_trace = tr.ctypes.data
+            o.max_sub = max_sub
         if peel_step is not None and self.m:
             o.d_peel_step = peel_step.data_ptr()
         rl = rs = None
@@ -214,6 +226,8 @@ class Graph:
         if record:
             k = min(int(st.sublevels), max_sub)
             res.append((rl[:k].copy(), rs[:k].copy()))
+        if trace:
+            res.append(tr[: min(int(st.sublevels), max_sub)].copy())
         if stats:
             res.append(st.as_dict())
         return res[0] if len(res) == 1 else tuple(res)

@@ -24,6 +24,8 @@
 //                     class
 //   fq[2]  3 x int32[m] per side of the curr/next ping-pong: light edges,
 //                     heavy edges, first chunk number of each heavy edge
+//   live[2] int32[m]  edges each Scan found above its level: the only edges
+//                     the next Scan visits (a list that shrinks level by level)
 //   ctr    int[...]   device counters (see peel.cu)
 #pragma once
 #include "common.cuh"
@@ -62,6 +64,7 @@ struct truss_graph {
     int2* ss = nullptr;
     int32_t* dmin = nullptr;
     int32_t* fq[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int32_t* live[2] = {nullptr, nullptr};  // live-edge lists of consecutive Scans
     int* ctr = nullptr;
     int* h_ctr = nullptr;  // pinned host mirror
     int latched = 0;       // latched device-side error status

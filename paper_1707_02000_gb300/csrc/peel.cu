@@ -42,21 +42,19 @@
 namespace {
 
 enum {
-    C_NL = 0,    // [0..3]   light-list size produced by phase p, slot p & 3
-    C_MIN = 4,   // [4..7]   minimum live support above l found by phase p
-    C_HC = 8,    // [8..15]  u64 per slot: heavy count << 32 | chunk total
-    C_BAR_COUNT = 16,
-    C_BAR_GEN = 17,
-    C_ERR = 18,
-    C_NSUB = 19,
-    C_NSCAN = 20,
-    C_NLEVEL = 21,
-    C_LAST_L = 22,
-    C_TRI = 24,  // [24..25] triangle count (u64), [26] max support
-    C_TOTAL = 32
+    C_SLOTS = 0,  // [0..31]  four SlotVals: what phase p produced, slot p & 3
+    C_BAR_COUNT = 32,  // grid-barrier arrivals since the launch began
+    C_ERR = 34,
+    C_NSUB = 35,
+    C_NSCAN = 36,
+    C_NLEVEL = 37,
+    C_LAST_L = 38,
+    C_TRI = 40,   // [40..41] triangle count (u64), [42] max support
+    C_TOTAL = 64
 };
 
 constexpr int PT = 256;      // threads per block in the peel kernels
+constexpr int PW = PT / 32;
 constexpr int LIGHT = 32;    // shorter row <= LIGHT entries: light edge
 constexpr int LCAP = 1024;   // per-block staging of light next-frontier appends
 constexpr int HCAP = PT;     // per-block staging of heavy appends (one per thread at flush)
@@ -74,7 +72,49 @@ struct PeelSmem {
     int lcnt, hcnt, lbase, hq0;
     uint32_t hb0;
     uint32_t wsum[PT / 32];
+    unsigned long long dsum;  // shorter-row lengths appended by this block
+    int dmax;
+    int wcnt[PW];             // block-wide append: per-warp counts, then offsets
+    int bbase;
+    int bmin[PW];
 };
+
+// Counters a phase fills in for the frontier it produces (32 bytes, read
+// back in one piece after the barrier that ends the phase).
+struct SlotVals {
+    int nl;                  // light-list size
+    int dmax;                // longest shorter row in the frontier
+    unsigned long long hc;   // heavy count << 32 | heavy chunk total
+    unsigned long long dsum; // sum of shorter-row lengths
+    int minv;                // minimum live support above l (Scan)
+    int nlive;               // live edges kept for the next Scan
+};
+static_assert(sizeof(SlotVals) == 32, "SlotVals is read as two 16-byte words");
+
+struct Slot {
+    int* nl;
+    unsigned long long* hc;
+    unsigned long long* dsum;
+    int* dmax;
+    int* minv;
+    int* nlive;
+};
+
+__host__ __device__ __forceinline__ SlotVals* slots(int* ctr) { return reinterpret_cast<SlotVals*>(ctr + C_SLOTS); }
+
+__host__ __device__ __forceinline__ Slot slot_of(int* ctr, int s) {
+    SlotVals* v = slots(ctr) + s;
+    return Slot{&v->nl, &v->hc, &v->dsum, &v->dmax, &v->minv, &v->nlive};
+}
+
+__host__ __device__ __forceinline__ void clear_slot_vals(SlotVals* v) {
+    v->nl = 0;
+    v->dmax = 0;
+    v->hc = 0ull;
+    v->dsum = 0ull;
+    v->minv = INT_MAX;
+    v->nlive = 0;
+}
 
 template <typename Off>
 struct Graph {
@@ -95,12 +135,15 @@ __device__ __forceinline__ uint32_t nchunks_of(int d, int hc) { return (uint32_t
 struct Appender {
     PeelSmem* sm;
     Frontier out;
-    int* nl;
-    unsigned long long* hcp;  // packed heavy counter
+    Slot cnt;
     const int32_t* dmin;
     int hc;
     __device__ __forceinline__ void push(int32_t f) const {
         const int d = __ldg(dmin + f);
+        atomicAdd(&sm->dsum, (unsigned long long)d);
+        atomicMax(&sm->dmax, d);
+        int* nl = cnt.nl;
+        unsigned long long* hcp = cnt.hc;
         if (d <= LIGHT) {
             const int p = atomicAdd(&sm->lcnt, 1);
             if (p < LCAP) {
@@ -122,6 +165,8 @@ struct Appender {
     }
     // whole block; leaves the stage empty
     __device__ void flush() const {
+        int* nl = cnt.nl;
+        unsigned long long* hcp = cnt.hc;
         __syncthreads();
         const int kl = min(sm->lcnt, LCAP), kh = min(sm->hcnt, HCAP);
         const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -141,6 +186,10 @@ struct Appender {
             total += sm->wsum[w];
         }
         if (t == 0) {
+            if (sm->dsum) {
+                atomicAdd(cnt.dsum, sm->dsum);
+                atomicMax(cnt.dmax, sm->dmax);
+            }
             sm->lbase = kl ? atomicAdd(nl, kl) : 0;
             if (kh) {
                 const unsigned long long old = atomicAdd(hcp, ((unsigned long long)kh << 32) | total);
@@ -158,10 +207,22 @@ struct Appender {
         if (t == 0) {
             sm->lcnt = 0;
             sm->hcnt = 0;
+            sm->dsum = 0;
+            sm->dmax = 0;
         }
         __syncthreads();
     }
 };
+
+__device__ __forceinline__ void smem_init(PeelSmem* sm) {
+    if (threadIdx.x == 0) {
+        sm->lcnt = 0;
+        sm->hcnt = 0;
+        sm->dsum = 0;
+        sm->dmax = 0;
+    }
+    __syncthreads();
+}
 
 __device__ __forceinline__ void relax(int2* ss, int32_t f, int32_t l, int32_t g, const Appender& ap) {
     int a = atomicSub(&ss[f].x, 1);
@@ -236,34 +297,60 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
             walk_rows<Off>(G, e1, r.a0, r.a1, r.b0, r.b1, sub, gsz, l, g, ap);
         }
     }
+    // heavy chunks: warp w takes the contiguous chunk range [c0, c1), so it
+    // looks up the owning edge once and then walks forward through the list
     const int lane = threadIdx.x & 31;
-    const int64_t nw = nth / 32;
-    for (int64_t w = gtid / 32; w < (int64_t)nchunk; w += nw) {
-        const int q = chunk_owner(cur.cbase, nh, (uint32_t)w);
-        const int32_t e1 = __ldcg(cur.heavy + q);
-        const Rows<Off> r = rows_of<Off>(G, e1);
-        const int64_t s0 = (int64_t)r.a0 + (w - (int64_t)__ldcg(cur.cbase + q)) * G.hc;
-        const int64_t s1 = min((int64_t)r.a1, s0 + G.hc);
-        walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r.b0, r.b1, lane, 32, l, g, ap);
+    const uint64_t nw = (uint64_t)(nth / 32), w = (uint64_t)(gtid / 32);
+    const uint32_t c0 = (uint32_t)((uint64_t)nchunk * w / nw), c1 = (uint32_t)((uint64_t)nchunk * (w + 1) / nw);
+    if (c0 < c1) {
+        int q = chunk_owner(cur.cbase, nh, c0);
+        uint32_t qb = __ldcg(cur.cbase + q);
+        uint32_t qn = q + 1 < nh ? __ldcg(cur.cbase + q + 1) : nchunk;
+        int32_t e1 = __ldcg(cur.heavy + q);
+        Rows<Off> r = rows_of<Off>(G, e1);
+        for (uint32_t c = c0; c < c1; c++) {
+            while (c >= qn) {  // every heavy edge owns at least one chunk
+                q++;
+                qb = qn;
+                qn = q + 1 < nh ? __ldcg(cur.cbase + q + 1) : nchunk;
+                e1 = __ldcg(cur.heavy + q);
+                r = rows_of<Off>(G, e1);
+            }
+            const int64_t s0 = (int64_t)r.a0 + (int64_t)(c - qb) * G.hc;
+            const int64_t s1 = min((int64_t)r.a1, s0 + (int64_t)G.hc);
+            walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r.b0, r.b1, lane, 32, l, g, ap);
+        }
     }
 }
 
-// Lanes per light edge for a sub-level: a whole warp per edge while that
-// still leaves most of the grid's warps busy, 8 lanes while there are a
-// few edges per group, one thread per edge on big frontiers.
+// Lanes per light edge for a sub-level (the variant).
 __host__ __device__ __forceinline__ int pick_group(int variant, int64_t nl, int64_t nthreads) {
     if (variant == TRUSS_VAR_THREAD) return 1;
     if (variant == TRUSS_VAR_GROUP) return 8;
-    if (variant == TRUSS_VAR_WARP) return 32;
-    if (nl * 32 <= nthreads) return 32;
-    if (nl * 8 <= 4 * nthreads) return 8;
-    return 1;
+    // default: measured on power-law and geometric graphs, a warp per light
+    // edge was the fastest choice in nearly every sub-level, small or large
+    (void)nl;
+    (void)nthreads;
+    return 32;
 }
 
 // Warp-aggregated append of matched edges to the light or heavy list.
 __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const int32_t* dmin, int hc,
-                                                     const Frontier& out, int* nl, unsigned long long* hcp) {
+                                                     const Frontier& out, const Slot& cnt) {
+    if (!__any_sync(FULL_MASK, hit)) return;
     const int d = hit ? __ldg(dmin + e) : 0;
+    {
+        unsigned long long sd = warp_sum((unsigned long long)d);
+        int md = d;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_xor_sync(FULL_MASK, md, o));
+        if (lane_id() == 0) {
+            atomicAdd(cnt.dsum, sd);
+            atomicMax(cnt.dmax, md);
+        }
+    }
+    int* nl = cnt.nl;
+    unsigned long long* hcp = cnt.hc;
     const bool light = hit && d <= LIGHT;
     warp_append(light, e, out.light, nl);
     const bool heavy = hit && !light;
@@ -289,49 +376,70 @@ __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const 
     }
 }
 
-// Scan at level l: curr <- {e : S[e] = l} split into light / heavy lists,
-// their stamps <- g; *minslot <- min(*minslot, min{S[e] : S[e] > l}).  Two
-// edges per 16-byte load.
-__device__ void scan_level(int2* ss, int64_t m, int32_t l, int32_t g, const Frontier out, int* nl,
-                           unsigned long long* hcp, int* minslot, const int32_t* dmin, int hc) {
-    const int64_t npair = (m + 1) / 2;
-    const int4* ss4 = reinterpret_cast<const int4*>(ss);
-    int mn = INT_MAX;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npair; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        int s0 = INT_MIN, s1 = INT_MIN;
-        if (p < npair) {
-            if (2 * p + 1 < m) {
-                int4 v = __ldcg(ss4 + p);
-                s0 = v.x;
-                s1 = v.z;
-            } else {
-                s0 = __ldcg(ss + 2 * p).x;
-            }
+// Block-wide append (all threads of the block call it together): one
+// atomic per block instead of one per warp.
+__device__ __forceinline__ void block_append(bool pred, int32_t v, int32_t* out, int* count, PeelSmem* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned b = __ballot_sync(FULL_MASK, pred);
+    if (lane == 0) sm->wcnt[warp] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < PW; w++) {
+            const int c = sm->wcnt[w];
+            sm->wcnt[w] = run;
+            run += c;
         }
-        const bool h0 = s0 == l, h1 = s1 == l;
-        if (h0) ss[2 * p].y = g;
-        if (h1) ss[2 * p + 1].y = g;
-        if (s0 > l) mn = min(mn, s0);
-        if (s1 > l) mn = min(mn, s1);
-        warp_classify_append(h0, (int32_t)(2 * p), dmin, hc, out, nl, hcp);
-        warp_classify_append(h1, (int32_t)(2 * p + 1), dmin, hc, out, nl, hcp);
+        sm->bbase = run ? atomicAdd(count, run) : 0;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
-    if (lane_id() == 0 && mn != INT_MAX) atomicMin(minslot, mn);
+    __syncthreads();
+    if (pred) out[sm->bbase + sm->wcnt[warp] + __popc(b & lanemask_lt())] = v;
+    __syncthreads();
 }
 
-__device__ __forceinline__ unsigned long long* hc_slot(int* ctr, int s) {
-    return reinterpret_cast<unsigned long long*>(ctr + C_HC) + s;
+// Scan at level l over the live edges: `in` lists them (nullptr: all m
+// edges, in id order).  curr <- {e : S[e] = l}, split into light / heavy
+// lists, their stamps <- g; edges with S > l are the live list of the next
+// Scan (`keep`); cnt.minv <- min(cnt.minv, min{S[e] : S[e] > l}).  Edges
+// below l are processed and drop out for good.
+__device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l, int32_t g,
+                           const Frontier out, const Slot& cnt, const int32_t* dmin, int hc, PeelSmem* sm) {
+    int mn = INT_MAX;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nin; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int32_t e = 0;
+        int sv = INT_MIN;
+        if (i < nin) {
+            e = in ? __ldcg(in + i) : (int32_t)i;
+            sv = __ldcg(&ss[e].x);
+        }
+        const bool hit = sv == l, live = sv > l;
+        if (hit) ss[e].y = g;
+        if (live) mn = min(mn, sv);
+        warp_classify_append(hit, e, dmin, hc, out, cnt);
+        block_append(live, e, keep, cnt.nlive, sm);
+    }
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
+    if (lane_id() == 0) sm->bmin[warp] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = INT_MAX;
+        for (int w = 0; w < PW; w++) b = min(b, sm->bmin[w]);
+        if (b != INT_MAX) atomicMin(cnt.minv, b);
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------- standalone kernels
 
-__global__ void __launch_bounds__(PT) k_scan(int2* ss, int64_t m, int32_t l, int32_t g, Frontier out, int* ctr,
-                                              const int32_t* dmin, int hc) {
-    scan_level(ss, m, l, g, out, ctr + C_NL, hc_slot(ctr, 0), ctr + C_MIN, dmin, hc);
+__global__ void __launch_bounds__(PT) k_scan(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l,
+                                              int32_t g, Frontier out, int* ctr, const int32_t* dmin, int hc) {
+    __shared__ PeelSmem sm;
+    smem_init(&sm);
+    scan_level(ss, in, nin, keep, l, g, out, slot_of(ctr, 0), dmin, hc, &sm);
 }
 
 // split a given edge list into light / heavy lists (state-level entry point)
@@ -340,7 +448,7 @@ __global__ void k_classify(const int32_t* __restrict__ edges, int64_t k, const i
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < k; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool hit = i < k;
-        warp_classify_append(hit, hit ? edges[i] : 0, dmin, hc, out, ctr + C_NL, hc_slot(ctr, 0));
+        warp_classify_append(hit, hit ? edges[i] : 0, dmin, hc, out, slot_of(ctr, 0));
     }
 }
 
@@ -350,49 +458,58 @@ template <typename Off>
 __global__ void __launch_bounds__(PT) k_process(Graph<Off> G, Frontier cur, int nl, int nh, uint32_t nchunk, int gsz,
                                                 int32_t l, int32_t g, Frontier nxt, int* ctr) {
     __shared__ PeelSmem sm;
-    if (threadIdx.x == 0) {
-        sm.lcnt = 0;
-        sm.hcnt = 0;
-    }
-    __syncthreads();
-    const Appender ap{&sm, nxt, ctr + C_NL + 1, hc_slot(ctr, 1), G.dmin, G.hc};
+    smem_init(&sm);
+    const Appender ap{&sm, nxt, slot_of(ctr, 1), G.dmin, G.hc};
     process_frontier<Off>(G, cur, nl, nh, nchunk, gsz, l, g, ap);
     ap.flush();
 }
 
 // ------------------------------------------------------------ grid barrier
 
-// Generation barrier over all blocks of a cooperative launch.  Every wait is
-// bounded: past timeout_ns the block records TRUSS_ETIMEOUT and returns
-// false; a block that sees an error recorded also returns false.
-__device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns) {
+// Barrier over all blocks of a cooperative launch.  One counter counts
+// arrivals since the launch began (never reset): the k-th barrier is passed
+// once it reaches k * nblocks.  Thread 0 arrives with one acq_rel atomic and
+// spins with acquire loads; it also copies the counter slot the next phase
+// needs into shared memory, so the block reads it without further round
+// trips.  Every wait is bounded: past timeout_ns the block records
+// TRUSS_ETIMEOUT and returns false; a block that sees an error recorded
+// also returns false.
+__device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns, unsigned& epoch, int read_slot,
+                             SlotVals* sv) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* count = reinterpret_cast<unsigned*>(ctr + C_BAR_COUNT);
-        unsigned* gen = reinterpret_cast<unsigned*>(ctr + C_BAR_GEN);
+        epoch += 1;
+        const unsigned target = epoch * nblocks;
+        unsigned v;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(count) : "memory");
+        v += 1;
         int ok = 1;
-        const unsigned my_gen = ld_acquire_gpu_u32(gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            st_release_gpu_u32(gen, my_gen + 1);
-        } else {
+        if ((int)(v - target) < 0) {
             const uint64_t t0 = global_ns();
-            while (ld_acquire_gpu_u32(gen) == my_gen) {
-                if (ld_acquire_gpu(ctr + C_ERR) != 0) { ok = 0; break; }
+            for (;;) {
+                __nanosleep(16);
+                v = ld_acquire_gpu_u32(count);
+                if ((int)(v - target) >= 0) break;
+                if (ld_acquire_gpu(ctr + C_ERR) != 0) {
+                    ok = 0;
+                    break;
+                }
                 if (global_ns() - t0 > timeout_ns) {
                     atomicCAS(ctr + C_ERR, 0, TRUSS_ETIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
             }
         }
-        __threadfence();
-        s_ok = ok && ld_acquire_gpu(ctr + C_ERR) == 0;
+        if (ok && read_slot >= 0) {
+            const int4* src = reinterpret_cast<const int4*>(slots(ctr) + read_slot);
+            int4* dst = reinterpret_cast<int4*>(sv);
+            dst[0] = __ldcg(src);
+            dst[1] = __ldcg(src + 1);
+        }
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -412,62 +529,75 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // and the barrier ending phase p-1 lies in between.
 template <typename Off>
 __global__ void __launch_bounds__(PT)
-    k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int* ctr, int variant, int level_jump, uint64_t timeout_ns,
-                 int32_t* rec_level, int64_t* rec_size, int64_t max_rec) {
+    k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
+                 int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace) {
     __shared__ PeelSmem sm;
-    if (threadIdx.x == 0) {
-        sm.lcnt = 0;
-        sm.hcnt = 0;
-    }
-    __syncthreads();
+    __shared__ __align__(16) SlotVals sv;
+    smem_init(&sm);
     const unsigned nblocks = gridDim.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned epoch = 0;
     int32_t l = 0, g = 0;
     int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0, p = 0;
-    auto clear_slot = [&](int64_t q) {
-        const int s = (int)(q & 3);
-        ctr[C_NL + s] = 0;
-        ctr[C_MIN + s] = INT_MAX;
-        *hc_slot(ctr, s) = 0ull;
-    };
+    int64_t nlive = G.m;  // edges the next Scan visits
+    uint64_t scan_ns = 0;
     while (processed < G.m) {
-        if (leader) clear_slot(p + 2);
+        uint64_t ts = 0;
+        if (leader) {
+            clear_slot_vals(slots(ctr) + ((p + 2) & 3));
+            ts = global_ns();
+        }
         const Frontier cur = (g & 1) ? f1 : f0;
-        const int s = (int)(p & 3);
-        scan_level(G.ss, G.m, l, g, cur, ctr + C_NL + s, hc_slot(ctr, s), ctr + C_MIN + s, G.dmin, G.hc);
-        if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-        int nl = ld_acquire_gpu(ctr + C_NL + s);
-        unsigned long long hcv = ld_acquire_u64(hc_slot(ctr, s));
-        const int mn = ld_acquire_gpu(ctr + C_MIN + s);
+        int s = (int)(p & 3);
+        const int32_t* lin = sc == 0 ? nullptr : ((sc & 1) ? live0 : live1);
+        int32_t* lout = (sc & 1) ? live1 : live0;
+        scan_level(G.ss, lin, nlive, lout, l, g, cur, slot_of(ctr, s), G.dmin, G.hc, &sm);
+        if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, s, &sv)) return;
+        if (leader) scan_ns += global_ns() - ts;
+        SlotVals v = sv;
+        nlive = v.nlive;
         p++;
         sc++;
-        if (nl + (int)(hcv >> 32) == 0) {
-            if (mn == INT_MAX) break;
-            l = level_jump ? mn : l + 1;
+        if (v.nl + (int)(v.hc >> 32) == 0) {
+            if (v.minv == INT_MAX) break;
+            l = level_jump ? v.minv : l + 1;
             continue;
         }
         nlevel++;
-        while (nl + (int)(hcv >> 32) > 0) {
-            const int nh = (int)(hcv >> 32);
-            const uint32_t nchunk = (uint32_t)hcv;
-            processed += nl + nh;
+        while (v.nl + (int)(v.hc >> 32) > 0) {
+            const int nl = v.nl;
+            const int nh = (int)(v.hc >> 32);
+            const uint32_t nchunk = (uint32_t)v.hc;
+            const int gsz = pick_group(variant, nl, nthreads);
             const int q = (int)(p & 3);
+            uint64_t t0 = 0;
             if (leader) {
-                if (nsub < max_rec) {
-                    rec_level[nsub] = l;
-                    rec_size[nsub] = nl + nh;
+                if (nsub < max_trace) {
+                    truss_sublevel_trace& r = trace[nsub];
+                    r.level = l;
+                    r.group = gsz;
+                    r.n_light = nl;
+                    r.n_heavy = nh;
+                    r.n_chunks = nchunk;
+                    r.dmax = v.dmax;
+                    r.dsum = (int64_t)v.dsum;
+                    r.todo = G.m - processed;
+                    r.scan_ns = (int64_t)scan_ns;
                 }
-                clear_slot(p + 2);
+                scan_ns = 0;
+                clear_slot_vals(slots(ctr) + ((p + 2) & 3));
+                t0 = global_ns();
             }
+            processed += nl + nh;
             const Frontier cu = (g & 1) ? f1 : f0;
             const Frontier nx = (g & 1) ? f0 : f1;
-            const Appender ap{&sm, nx, ctr + C_NL + q, hc_slot(ctr, q), G.dmin, G.hc};
-            process_frontier<Off>(G, cu, nl, nh, nchunk, pick_group(variant, nl, nthreads), l, g, ap);
+            const Appender ap{&sm, nx, slot_of(ctr, q), G.dmin, G.hc};
+            process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
             ap.flush();
-            if (!grid_barrier(ctr, nblocks, timeout_ns)) return;
-            nl = ld_acquire_gpu(ctr + C_NL + q);
-            hcv = ld_acquire_u64(hc_slot(ctr, q));
+            if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, q, &sv)) return;
+            if (leader && nsub < max_trace) trace[nsub].t_ns = (int64_t)(global_ns() - t0);
+            v = sv;
             p++;
             g++;
             nsub++;
@@ -513,9 +643,14 @@ __global__ void k_sum_support(const int2* __restrict__ ss, int64_t m, unsigned l
     }
 }
 
+__global__ void k_clear_slot(int* ctr, int q) {
+    if (threadIdx.x == 0) clear_slot_vals(slots(ctr) + q);
+}
+
 __global__ void k_init_counters(int* ctr) {
-    int i = threadIdx.x;
-    if (i < C_TOTAL) ctr[i] = (i >= C_MIN && i < C_MIN + 4) ? INT_MAX : 0;
+    for (int i = threadIdx.x; i < C_TOTAL; i += blockDim.x) ctr[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < 4) clear_slot_vals(slots(ctr) + threadIdx.x);
 }
 
 // state import for truss_peel_sublevel: canonical (S, flags) -> internal ss
@@ -589,10 +724,11 @@ struct RunOut {
 };
 
 // Algorithm 4's loop driven from the host: one Scan launch per level, one
-// ProcessSubLevel launch per sub-level, the frontier sizes read back after each.
+// ProcessSubLevel launch per sub-level, the frontier sizes read back after
+// each.  trace (host, may be NULL) receives max_trace sub-level records.
 template <typename Off>
-int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, std::vector<int32_t>* rl,
-              std::vector<int64_t>* rs, RunOut* out) {
+int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* trace, int64_t max_trace,
+              RunOut* out) {
     Graph<Off> G = graph_view<Off>(g);
     int* ctr = g->ctr;
     int* h = g->h_ctr;
@@ -600,72 +736,103 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, std::vector<i
     const int pmax = process_blocks<Off>(g);
     int32_t l = 0, gs = 0;
     int64_t processed = 0;
-    auto read_slot = [&](int slot, int* nl, int* nh, uint32_t* nc) {
-        unsigned long long v;
-        memcpy(&v, h + C_HC + 2 * slot, sizeof(v));
-        *nl = h[C_NL + slot];
-        *nh = (int)(v >> 32);
-        *nc = (uint32_t)v;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (trace) {
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+    }
+    auto read_slot = [&](int slot, int* nl, int* nh, uint32_t* nc, int64_t* dsum, int* dmax) {
+        SlotVals v;
+        memcpy(&v, slots(h) + slot, sizeof(v));
+        *nl = v.nl;
+        *nh = (int)(v.hc >> 32);
+        *nc = (uint32_t)v.hc;
+        *dsum = (int64_t)v.dsum;
+        *dmax = v.dmax;
     };
-    while (processed < g->m) {
-        k_init_counters<<<1, 32, 0, s>>>(ctr);
-        k_scan<<<sblocks, PT, 0, s>>>(g->ss, g->m, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc);
+    int rc = TRUSS_OK;
+    int64_t nlive = g->m, scan_ns = 0;
+    while (processed < g->m && rc == TRUSS_OK) {
+        const int32_t* lin = out->nscan == 0 ? nullptr : g->live[(out->nscan + 1) & 1];
+        int32_t* lout = g->live[out->nscan & 1];
+        k_init_counters<<<1, 64, 0, s>>>(ctr);
+        if (trace) CU(cudaEventRecord(e0, s));
+        k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc);
+        if (trace) CU(cudaEventRecord(e1, s));
         CU(cudaGetLastError());
         truss_note_launch(2);
         CU(cudaMemcpyAsync(h, ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
+        if (trace) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            scan_ns += (int64_t)(ms * 1e6);
+        }
+        nlive = slots(h)[0].nlive;
         out->nscan++;
-        int nl, nh;
+        int nl, nh, dmax;
         uint32_t nc;
-        read_slot(0, &nl, &nh, &nc);
+        int64_t dsum;
+        read_slot(0, &nl, &nh, &nc, &dsum, &dmax);
         if (nl + nh == 0) {
-            if (h[C_MIN] == INT_MAX) break;
-            l = o.level_jump ? h[C_MIN] : l + 1;
+            const int mn = slots(h)[0].minv;
+            if (mn == INT_MAX) break;
+            l = o.level_jump ? mn : l + 1;
             continue;
         }
         out->nlevel++;
         while (nl + nh > 0) {
+            const int gsz = pick_group(o.variant, nl, (int64_t)pmax * PT);
+            truss_sublevel_trace* r = (trace && out->nsub < max_trace) ? trace + out->nsub : nullptr;
+            if (r) *r = truss_sublevel_trace{l, gsz, nl, nh, nc, dmax, dsum, g->m - processed, 0, scan_ns};
+            scan_ns = 0;
             processed += nl + nh;
-            if (rl) {
-                rl->push_back(l);
-                rs->push_back(nl + nh);
-            }
-            // next lists are counted in slot 1
-            CU(cudaMemsetAsync(ctr + C_NL + 1, 0, sizeof(int), s));
-            CU(cudaMemsetAsync(ctr + C_HC + 2, 0, sizeof(unsigned long long), s));
-            const int gmax = pick_group(o.variant, nl, (int64_t)pmax * PT);
-            const int64_t want = std::max<int64_t>(((int64_t)nl * gmax + PT - 1) / PT, ((int64_t)nc * 32 + PT - 1) / PT);
+            // the next frontier is counted in slot 1
+            k_clear_slot<<<1, 32, 0, s>>>(ctr, 1);
+            const int64_t want = std::max<int64_t>(((int64_t)nl * gsz + PT - 1) / PT, ((int64_t)nc * 32 + PT - 1) / PT);
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(pmax, want));
-            k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, gs & 1), nl, nh, nc, gmax, l, gs, side(g, (gs + 1) & 1), ctr);
+            if (r) CU(cudaEventRecord(e0, s));
+            k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, gs & 1), nl, nh, nc, gsz, l, gs, side(g, (gs + 1) & 1), ctr);
+            if (r) CU(cudaEventRecord(e1, s));
             CU(cudaGetLastError());
-            truss_note_launch();
+            truss_note_launch(2);
             CU(cudaMemcpyAsync(h, ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
-            read_slot(1, &nl, &nh, &nc);
+            if (r) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                r->t_ns = (int64_t)(ms * 1e6);
+            }
+            read_slot(1, &nl, &nh, &nc, &dsum, &dmax);
             gs++;
             out->nsub++;
         }
         l++;
     }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     out->last_l = l;
-    return TRUSS_OK;
+    return rc;
 }
 
 template <typename Off>
-int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, int32_t* d_rl, int64_t* d_rs, int64_t max_rec) {
+int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
+                   int64_t max_trace) {
     Graph<Off> G = graph_view<Off>(g);
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<Off>, PT, 0));
     if (per_sm < 1) return TRUSS_ENOTSUP;
     int blocks = per_sm * g->sms;
-    k_init_counters<<<1, 32, 0, s>>>(g->ctr);
+    k_init_counters<<<1, 64, 0, s>>>(g->ctr);
     CU(cudaGetLastError());
     int variant = o.variant;
     int jump = o.level_jump;
     uint64_t tmo = o.timeout_ns > 0 ? (uint64_t)o.timeout_ns : 10000000000ull;
     Frontier f0 = side(g, 0), f1 = side(g, 1);
+    int32_t* live0 = g->live[0];
+    int32_t* live1 = g->live[1];
     int* ctr = g->ctr;
-    void* args[] = {&G, &f0, &f1, &ctr, &variant, &jump, &tmo, &d_rl, &d_rs, &max_rec};
+    void* args[] = {&G, &f0, &f1, &live0, &live1, &ctr, &variant, &jump, &tmo, &d_trace, &max_trace};
     CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off>, dim3(blocks), dim3(PT), args, 0, s));
     truss_note_launch(2);
     return TRUSS_OK;
@@ -674,8 +841,8 @@ int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, int32_t*
 int check_opts(const truss_opts& o) {
     if (o.loop != TRUSS_LOOP_PLAIN && o.loop != TRUSS_LOOP_PERSISTENT) return TRUSS_EINVAL;
     if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_WARP) return TRUSS_EINVAL;
-    if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size || o.max_sub < 0 || !o.sync))
-        return TRUSS_EINVAL;
+    if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size)) return TRUSS_EINVAL;
+    if ((o.h_sub_level || o.h_trace) && (o.max_sub < 0 || !o.sync)) return TRUSS_EINVAL;
     return TRUSS_OK;
 }
 
@@ -699,20 +866,15 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
     }
     if (timed) CU(cudaEventRecord(ev[1], s));
     RunOut ro;
-    std::vector<int32_t> rl;
-    std::vector<int64_t> rs;
-    const bool rec = o.h_sub_level && o.max_sub > 0;
+    const bool rec = (o.h_sub_level || o.h_trace) && o.max_sub > 0;
+    std::vector<truss_sublevel_trace> htr(rec ? (size_t)o.max_sub : 0);
     int rc = TRUSS_OK;
     if (o.loop == TRUSS_LOOP_PLAIN) {
-        rc = run_plain<Off>(g, o, s, rec ? &rl : nullptr, rec ? &rs : nullptr, &ro);
+        rc = run_plain<Off>(g, o, s, rec ? htr.data() : nullptr, rec ? o.max_sub : 0, &ro);
     } else {
-        int32_t* d_rl = nullptr;
-        int64_t* d_rs = nullptr;
-        if (rec) {
-            CU(cudaMallocAsync((void**)&d_rl, sizeof(int32_t) * (size_t)o.max_sub, s));
-            CU(cudaMallocAsync((void**)&d_rs, sizeof(int64_t) * (size_t)o.max_sub, s));
-        }
-        rc = run_persistent<Off>(g, o, s, d_rl, d_rs, rec ? o.max_sub : 0);
+        truss_sublevel_trace* d_tr = nullptr;
+        if (rec) CU(cudaMallocAsync((void**)&d_tr, sizeof(truss_sublevel_trace) * (size_t)o.max_sub, s));
+        rc = run_persistent<Off>(g, o, s, d_tr, rec ? o.max_sub : 0);
         if (rc == TRUSS_OK && o.sync) {
             CU(cudaMemcpyAsync(g->h_ctr, g->ctr, sizeof(int) * C_TRI, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
@@ -722,13 +884,11 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             ro.nlevel = g->h_ctr[C_NLEVEL];
             ro.last_l = g->h_ctr[C_LAST_L];
             if (rec && rc == TRUSS_OK) {
-                int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
-                CU(cudaMemcpyAsync(o.h_sub_level, d_rl, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
-                CU(cudaMemcpyAsync(o.h_sub_size, d_rs, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
+                const int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
+                CU(cudaMemcpyAsync(htr.data(), d_tr, sizeof(truss_sublevel_trace) * (size_t)k, cudaMemcpyDeviceToHost, s));
             }
         }
-        if (d_rl) cudaFreeAsync(d_rl, s);
-        if (d_rs) cudaFreeAsync(d_rs, s);
+        if (d_tr) cudaFreeAsync(d_tr, s);
     }
     if (rc != TRUSS_OK) {
         if (timed)
@@ -747,10 +907,15 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
     CU(cudaGetLastError());
     if (o.sync) {
         CU(cudaStreamSynchronize(s));
-        if (rec && o.loop == TRUSS_LOOP_PLAIN) {
-            int64_t k = std::min<int64_t>((int64_t)rl.size(), o.max_sub);
-            std::copy(rl.begin(), rl.begin() + k, o.h_sub_level);
-            std::copy(rs.begin(), rs.begin() + k, o.h_sub_size);
+        if (rec) {
+            const int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
+            for (int64_t i = 0; i < k; i++) {
+                if (o.h_sub_level) {
+                    o.h_sub_level[i] = htr[i].level;
+                    o.h_sub_size[i] = (int64_t)htr[i].n_light + htr[i].n_heavy;
+                }
+                if (o.h_trace) o.h_trace[i] = htr[i];
+            }
         }
     }
     if (st) {
@@ -791,7 +956,7 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
         k_inverse_perm<<<grid_for(m, 256), 256, 0, s>>>(g->perm, m, inv);
     }
     k_import_state<<<grid_for(m, 256), 256, 0, s>>>(d_S, d_flags, g->perm, m, g->ss);
-    k_init_counters<<<1, 32, 0, s>>>(g->ctr);
+    k_init_counters<<<1, 64, 0, s>>>(g->ctr);
     if (ncurr > 0) {
         k_map_ids<<<grid_for(ncurr, 256), 256, 0, s>>>(d_curr, ncurr, inv, cur);
         k_mark_curr<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->ss);
@@ -801,10 +966,10 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
     int* h = g->h_ctr;
     CU(cudaMemcpyAsync(h, g->ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    unsigned long long v;
-    memcpy(&v, h + C_HC, sizeof(v));
-    const int nl = h[C_NL], nh = (int)(v >> 32);
-    const uint32_t nc = (uint32_t)v;
+    SlotVals v0;
+    memcpy(&v0, slots(h), sizeof(v0));
+    const int nl = v0.nl, nh = (int)(v0.hc >> 32);
+    const uint32_t nc = (uint32_t)v0.hc;
     if (nl + nh > 0) {
         Graph<Off> G = graph_view<Off>(g);
         const int blocks = process_blocks<Off>(g);
@@ -814,8 +979,9 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
     }
     CU(cudaMemcpyAsync(h, g->ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    memcpy(&v, h + C_HC + 2, sizeof(v));
-    const int nl1 = h[C_NL + 1], nh1 = (int)(v >> 32);
+    SlotVals v1;
+    memcpy(&v1, slots(h) + 1, sizeof(v1));
+    const int nl1 = v1.nl, nh1 = (int)(v1.hc >> 32);
     if (nl1 > 0) k_map_ids<<<grid_for(nl1, 256), 256, 0, s>>>(g->fq[1][0], nl1, g->perm, d_next);
     if (nh1 > 0) k_map_ids<<<grid_for(nh1, 256), 256, 0, s>>>(g->fq[1][1], nh1, g->perm, d_next + nl1);
     k_export_state<<<grid_for(m, 256), 256, 0, s>>>(g->ss, g->perm, m, d_S, d_flags);
@@ -832,15 +998,17 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 int truss_ensure_workspace(truss_graph* g) {
     if (g->ctr) return TRUSS_OK;
     const size_t m = (size_t)(g->m > 0 ? g->m : 1);
-    // heavy chunk length: 64 entries, longer when the graph is so large that
+    // heavy chunk length: 32 entries, longer when the graph is so large that
     // a sub-level's chunk total could leave 32 bits
-    int64_t hc = 64;
+    int64_t hc = 32;
     while ((int64_t)g->m + g->dmin_sum / hc >= ((int64_t)1 << 32) - 1) hc *= 2;
     g->hc = (int)hc;
     CU(cudaMalloc((void**)&g->ss, sizeof(int2) * (m + 1)));
     CU(cudaMalloc((void**)&g->dmin, sizeof(int32_t) * m));
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) CU(cudaMalloc((void**)&g->fq[k][j], sizeof(int32_t) * m));
+        CU(cudaMalloc((void**)&g->live[k], sizeof(int32_t) * m));
+    }
     CU(cudaMalloc((void**)&g->ctr, sizeof(int) * C_TOTAL));
     CU(cudaMallocHost((void**)&g->h_ctr, sizeof(int) * C_TOTAL));
     if (g->m > 0) {
@@ -857,11 +1025,14 @@ int truss_ensure_workspace(truss_graph* g) {
 void truss_release_workspace(truss_graph* g) {
     cudaFree(g->ss);
     cudaFree(g->dmin);
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) {
             cudaFree(g->fq[k][j]);
             g->fq[k][j] = nullptr;
         }
+        cudaFree(g->live[k]);
+        g->live[k] = nullptr;
+    }
     cudaFree(g->ctr);
     cudaFreeHost(g->h_ctr);
     g->ss = nullptr;

@@ -333,3 +333,26 @@ def test_peel_steps_match_serial_run_and_certify(pkt, loop):
         assert np.array_equal(tau, want), name
         assert np.array_equal(host(step), ostep), name
         assert oracle.certify(g.n, eu, ev, tau, host(step))[0] == 0
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_sublevel_trace(pkt, loop):
+    """The per-sub-level trace agrees with the recorded frontier sequence and
+    with the graph: sizes sum to m, todo counts down, lane groups are valid,
+    dsum/dmax match the frontier's shorter-row lengths."""
+    g = gg.chung_lu(4000, 2.1, 16.0, 400.0, seed=11)
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    tau, (lv, sz), tr = G.decompose(loop=_loop(pkt, loop), record=True, trace=True)
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    want, olv, osz, step = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+    assert np.array_equal(host(tau), want)
+    assert np.array_equal(tr["level"], olv) and np.array_equal(tr["n_light"] + tr["n_heavy"], osz)
+    assert np.array_equal(tr["todo"], eu.size - np.concatenate([[0], np.cumsum(osz)[:-1]]))
+    assert set(np.unique(tr["group"])) <= {1, 8, 32}
+    assert np.all(tr["t_ns"] > 0) and tr["scan_ns"][0] > 0 and np.all(tr["scan_ns"] >= 0)
+    deg = np.bincount(np.concatenate([eu, ev]), minlength=g.n)
+    dmin = np.minimum(deg[eu], deg[ev])
+    for k in range(len(tr)):
+        sel = step == k
+        assert tr["dsum"][k] == int(dmin[sel].sum()) and tr["dmax"][k] == int(dmin[sel].max())
+        assert tr["n_light"][k] == int((dmin[sel] <= 32).sum())
