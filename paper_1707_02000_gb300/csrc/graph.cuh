@@ -26,6 +26,7 @@
 //                     heavy edges, first chunk number of each heavy edge
 //   live[2] int32[m]  edges each Scan found above its level: the only edges
 //                     the next Scan visits (a list that shrinks level by level)
+//   owner[2] uint32   chunk -> heavy-list position for each frontier side
 //   ctr    int[...]   device counters (see peel.cu)
 #pragma once
 #include "common.cuh"
@@ -65,6 +66,8 @@ struct truss_graph {
     int32_t* dmin = nullptr;
     int32_t* fq[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int32_t* live[2] = {nullptr, nullptr};  // live-edge lists of consecutive Scans
+    uint32_t* owner[2] = {nullptr, nullptr}; // chunk -> heavy-list position, per side
+    uint32_t ocap = 0;
     int* ctr = nullptr;
     int* h_ctr = nullptr;  // pinned host mirror
     int latched = 0;       // latched device-side error status

@@ -64,6 +64,7 @@ struct Frontier {
     int32_t* light;
     int32_t* heavy;
     uint32_t* cbase;  // first chunk number of each heavy edge (monotone)
+    uint32_t* owner;  // heavy-list position owning each chunk (if the total fits ocap)
 };
 
 struct PeelSmem {
@@ -126,18 +127,24 @@ struct Graph {
     int2* ss;
     int64_t m;
     int hc;  // heavy chunk length (entries of the shorter row)
+    uint32_t ocap;                     // capacity of each side's chunk owner map
 };
 
 __device__ __forceinline__ uint32_t nchunks_of(int d, int hc) { return (uint32_t)((d + hc - 1) / hc); }
 
-// Next-frontier append, staged per block in shared memory; a full stage
-// spills straight to the global lists.
+// owner[base .. base + n) = q when that range fits the map
+__device__ __forceinline__ void write_owner(const Frontier& out, uint32_t ocap, uint32_t base, uint32_t n, int q) {
+    if ((uint64_t)base + n <= ocap)
+        for (uint32_t k = 0; k < n; k++) out.owner[base + k] = (uint32_t)q;
+}
+
 struct Appender {
     PeelSmem* sm;
     Frontier out;
     Slot cnt;
     const int32_t* dmin;
     int hc;
+    uint32_t ocap;
     __device__ __forceinline__ void push(int32_t f) const {
         const int d = __ldg(dmin + f);
         atomicAdd(&sm->dsum, (unsigned long long)d);
@@ -156,10 +163,12 @@ struct Appender {
             if (p < HCAP) {
                 sm->hbuf[p] = f;
             } else {
-                const unsigned long long old = atomicAdd(hcp, (1ull << 32) | nchunks_of(d, hc));
+                const uint32_t nch = nchunks_of(d, hc);
+                const unsigned long long old = atomicAdd(hcp, (1ull << 32) | nch);
                 const int q = (int)(old >> 32);
                 out.heavy[q] = f;
                 out.cbase[q] = (uint32_t)old;
+                write_owner(out, ocap, (uint32_t)old, nch, q);
             }
         }
     }
@@ -202,6 +211,7 @@ struct Appender {
         if (t < kh) {
             out.heavy[sm->hq0 + t] = sm->hbuf[t];
             out.cbase[sm->hq0 + t] = sm->hb0 + before + x - c;
+            write_owner(out, ocap, sm->hb0 + before + x - c, c, sm->hq0 + t);
         }
         __syncthreads();
         if (t == 0) {
@@ -260,13 +270,14 @@ __device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
 }
 
 // All triangles through e1 whose apex is one of the slots start, start+step,
-// ... of [a0, a1) (part of the shorter row), probed in the longer row [b0, b1).
+// ... of [a0, a1) (part of the shorter row), each probed in the longer row
+// by binary search.
 template <typename Off>
-__device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a0, Off a1, Off b0, Off b1, int start,
-                                          int step, int32_t l, int32_t g, const Appender& ap) {
+__device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a0, Off a1, const Rows<Off>& r,
+                                          int start, int step, int32_t l, int32_t g, const Appender& ap) {
     for (Off j = a0 + start; j < a1; j += step) {
         int32_t w = __ldg(G.col + j);
-        Off q = find_dev<Off>(G.col, b0, b1, w);
+        Off q = find_dev<Off>(G.col, r.b0, r.b1, w);
         if (q >= 0) on_triangle(G.ss, e1, __ldg(G.eid + j), __ldg(G.eid + q), l, g, ap);
     }
 }
@@ -294,7 +305,7 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
         for (int64_t i = gtid / gsz; i < nl; i += ngrp) {
             const int32_t e1 = __ldcg(cur.light + i);
             const Rows<Off> r = rows_of<Off>(G, e1);
-            walk_rows<Off>(G, e1, r.a0, r.a1, r.b0, r.b1, sub, gsz, l, g, ap);
+            walk_rows<Off>(G, e1, r.a0, r.a1, r, sub, gsz, l, g, ap);
         }
     }
     // heavy chunks: warp w takes the contiguous chunk range [c0, c1), so it
@@ -303,7 +314,7 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
     const uint64_t nw = (uint64_t)(nth / 32), w = (uint64_t)(gtid / 32);
     const uint32_t c0 = (uint32_t)((uint64_t)nchunk * w / nw), c1 = (uint32_t)((uint64_t)nchunk * (w + 1) / nw);
     if (c0 < c1) {
-        int q = chunk_owner(cur.cbase, nh, c0);
+        int q = nchunk <= G.ocap ? (int)__ldcg(cur.owner + c0) : chunk_owner(cur.cbase, nh, c0);
         uint32_t qb = __ldcg(cur.cbase + q);
         uint32_t qn = q + 1 < nh ? __ldcg(cur.cbase + q + 1) : nchunk;
         int32_t e1 = __ldcg(cur.heavy + q);
@@ -318,7 +329,7 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
             }
             const int64_t s0 = (int64_t)r.a0 + (int64_t)(c - qb) * G.hc;
             const int64_t s1 = min((int64_t)r.a1, s0 + (int64_t)G.hc);
-            walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r.b0, r.b1, lane, 32, l, g, ap);
+            walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r, lane, 32, l, g, ap);
         }
     }
 }
@@ -335,7 +346,7 @@ __host__ __device__ __forceinline__ int pick_group(int variant, int64_t nl, int6
 }
 
 // Warp-aggregated append of matched edges to the light or heavy list.
-__device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const int32_t* dmin, int hc,
+__device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const int32_t* dmin, int hc, uint32_t ocap,
                                                      const Frontier& out, const Slot& cnt) {
     if (!__any_sync(FULL_MASK, hit)) return;
     const int d = hit ? __ldg(dmin + e) : 0;
@@ -372,6 +383,7 @@ __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const 
             const int q = (int)(old >> 32) + __popc(b & lanemask_lt());
             out.heavy[q] = e;
             out.cbase[q] = (uint32_t)old + x - c;
+            write_owner(out, ocap, (uint32_t)old + x - c, c, q);
         }
     }
 }
@@ -403,7 +415,8 @@ __device__ __forceinline__ void block_append(bool pred, int32_t v, int32_t* out,
 // Scan (`keep`); cnt.minv <- min(cnt.minv, min{S[e] : S[e] > l}).  Edges
 // below l are processed and drop out for good.
 __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l, int32_t g,
-                           const Frontier out, const Slot& cnt, const int32_t* dmin, int hc, PeelSmem* sm) {
+                           const Frontier out, const Slot& cnt, const int32_t* dmin, int hc, uint32_t ocap,
+                           PeelSmem* sm) {
     int mn = INT_MAX;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nin; base += stride) {
@@ -417,7 +430,7 @@ __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* ke
         const bool hit = sv == l, live = sv > l;
         if (hit) ss[e].y = g;
         if (live) mn = min(mn, sv);
-        warp_classify_append(hit, e, dmin, hc, out, cnt);
+        warp_classify_append(hit, e, dmin, hc, ocap, out, cnt);
         block_append(live, e, keep, cnt.nlive, sm);
     }
     const int warp = threadIdx.x >> 5;
@@ -436,19 +449,20 @@ __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* ke
 // ------------------------------------------------------- standalone kernels
 
 __global__ void __launch_bounds__(PT) k_scan(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l,
-                                              int32_t g, Frontier out, int* ctr, const int32_t* dmin, int hc) {
+                                              int32_t g, Frontier out, int* ctr, const int32_t* dmin, int hc,
+                                              uint32_t ocap) {
     __shared__ PeelSmem sm;
     smem_init(&sm);
-    scan_level(ss, in, nin, keep, l, g, out, slot_of(ctr, 0), dmin, hc, &sm);
+    scan_level(ss, in, nin, keep, l, g, out, slot_of(ctr, 0), dmin, hc, ocap, &sm);
 }
 
 // split a given edge list into light / heavy lists (state-level entry point)
-__global__ void k_classify(const int32_t* __restrict__ edges, int64_t k, const int32_t* dmin, int hc, Frontier out,
-                           int* ctr) {
+__global__ void k_classify(const int32_t* __restrict__ edges, int64_t k, const int32_t* dmin, int hc, uint32_t ocap,
+                           Frontier out, int* ctr) {
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < k; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool hit = i < k;
-        warp_classify_append(hit, hit ? edges[i] : 0, dmin, hc, out, slot_of(ctr, 0));
+        warp_classify_append(hit, hit ? edges[i] : 0, dmin, hc, ocap, out, slot_of(ctr, 0));
     }
 }
 
@@ -459,7 +473,7 @@ __global__ void __launch_bounds__(PT) k_process(Graph<Off> G, Frontier cur, int 
                                                 int32_t l, int32_t g, Frontier nxt, int* ctr) {
     __shared__ PeelSmem sm;
     smem_init(&sm);
-    const Appender ap{&sm, nxt, slot_of(ctr, 1), G.dmin, G.hc};
+    const Appender ap{&sm, nxt, slot_of(ctr, 1), G.dmin, G.hc, G.ocap};
     process_frontier<Off>(G, cur, nl, nh, nchunk, gsz, l, g, ap);
     ap.flush();
 }
@@ -527,8 +541,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // writes its counters to slot p & 3; slot (p+2) & 3 is cleared during phase
 // p: its last readers read it right after the barrier that ended phase p-2,
 // and the barrier ending phase p-1 lies in between.
+// Six blocks per SM (at most 40 registers): measured against 4-8 blocks on
+// the power-law and geometric workloads, it balances occupancy for big
+// throughput-bound frontiers against spills on the latency-bound path.
 template <typename Off>
-__global__ void __launch_bounds__(PT)
+__global__ void __launch_bounds__(PT, 6)
     k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
                  int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace) {
     __shared__ PeelSmem sm;
@@ -552,7 +569,7 @@ __global__ void __launch_bounds__(PT)
         int s = (int)(p & 3);
         const int32_t* lin = sc == 0 ? nullptr : ((sc & 1) ? live0 : live1);
         int32_t* lout = (sc & 1) ? live1 : live0;
-        scan_level(G.ss, lin, nlive, lout, l, g, cur, slot_of(ctr, s), G.dmin, G.hc, &sm);
+        scan_level(G.ss, lin, nlive, lout, l, g, cur, slot_of(ctr, s), G.dmin, G.hc, G.ocap, &sm);
         if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, s, &sv)) return;
         if (leader) scan_ns += global_ns() - ts;
         SlotVals v = sv;
@@ -592,7 +609,7 @@ __global__ void __launch_bounds__(PT)
             processed += nl + nh;
             const Frontier cu = (g & 1) ? f1 : f0;
             const Frontier nx = (g & 1) ? f0 : f1;
-            const Appender ap{&sm, nx, slot_of(ctr, q), G.dmin, G.hc};
+            const Appender ap{&sm, nx, slot_of(ctr, q), G.dmin, G.hc, G.ocap};
             process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
             ap.flush();
             if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, q, &sv)) return;
@@ -711,11 +728,11 @@ int process_blocks(const truss_graph* g) {
 
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
-    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, g->ss, g->m, g->hc};
+    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, g->ss, g->m, g->hc, g->ocap};
 }
 
 Frontier side(truss_graph* g, int k) {
-    return Frontier{g->fq[k][0], g->fq[k][1], reinterpret_cast<uint32_t*>(g->fq[k][2])};
+    return Frontier{g->fq[k][0], g->fq[k][1], reinterpret_cast<uint32_t*>(g->fq[k][2]), g->owner[k]};
 }
 
 struct RunOut {
@@ -757,7 +774,7 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
         int32_t* lout = g->live[out->nscan & 1];
         k_init_counters<<<1, 64, 0, s>>>(ctr);
         if (trace) CU(cudaEventRecord(e0, s));
-        k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc);
+        k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc, g->ocap);
         if (trace) CU(cudaEventRecord(e1, s));
         CU(cudaGetLastError());
         truss_note_launch(2);
@@ -960,7 +977,7 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
     if (ncurr > 0) {
         k_map_ids<<<grid_for(ncurr, 256), 256, 0, s>>>(d_curr, ncurr, inv, cur);
         k_mark_curr<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->ss);
-        k_classify<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->dmin, g->hc, side(g, 0), g->ctr);
+        k_classify<<<grid_for(ncurr, 256), 256, 0, s>>>(cur, ncurr, g->dmin, g->hc, g->ocap, side(g, 0), g->ctr);
     }
     CU(cudaGetLastError());
     int* h = g->h_ctr;
@@ -1011,6 +1028,14 @@ int truss_ensure_workspace(truss_graph* g) {
     }
     CU(cudaMalloc((void**)&g->ctr, sizeof(int) * C_TOTAL));
     CU(cudaMallocHost((void**)&g->h_ctr, sizeof(int) * C_TOTAL));
+    // chunk owner maps: enough for any sub-level of graphs up to moderate
+    // size; larger chunk totals fall back to a search
+    {
+        const int64_t want = (int64_t)g->m + g->dmin_sum / hc + 1;
+        const int64_t cap = std::min<int64_t>(want, std::min<int64_t>(4 * (int64_t)g->m + 1024, (int64_t)UINT32_MAX));
+        g->ocap = (uint32_t)cap;
+        for (int k = 0; k < 2; k++) CU(cudaMalloc((void**)&g->owner[k], sizeof(uint32_t) * (size_t)cap));
+    }
     if (g->m > 0) {
         if (g->off64)
             k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin);
@@ -1035,6 +1060,10 @@ void truss_release_workspace(truss_graph* g) {
     }
     cudaFree(g->ctr);
     cudaFreeHost(g->h_ctr);
+    for (int k = 0; k < 2; k++) {
+        cudaFree(g->owner[k]);
+        g->owner[k] = nullptr;
+    }
     g->ss = nullptr;
     g->dmin = nullptr;
     g->ctr = nullptr;

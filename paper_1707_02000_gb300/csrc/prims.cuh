@@ -124,7 +124,7 @@ constexpr int RS_ROUNDS = 16;                      // 32-key rounds per warp
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;    // keys per block
 constexpr int RS_RADIX = 256;
 
-__global__ void __launch_bounds__(RS_THREADS)
+static __global__ void __launch_bounds__(RS_THREADS)
     rs_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[RS_RADIX];
     h[threadIdx.x] = 0;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(RS_THREADS)
 // Stable scatter: warp w of a block owns keys [w*512, (w+1)*512) of the tile
 // and walks them 32 at a time in order; equal digits inside a round are
 // ranked by lane (match.any), and earlier rounds / warps / blocks come first.
-__global__ void __launch_bounds__(RS_THREADS)
+static __global__ void __launch_bounds__(RS_THREADS)
     rs_scatter_kernel(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out, int64_t n, int shift,
                       const uint32_t* __restrict__ offsets) {
     __shared__ uint32_t cnt[RS_WARPS][RS_RADIX];
