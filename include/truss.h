@@ -242,6 +242,31 @@ TRUSS_API int truss_decompose_host(const int32_t* h_src, const int32_t* h_dst, i
                          int32_t* h_truss, int64_t m_cap, int64_t* m_out, const truss_opts* opts,
                          truss_stats* stats, void* stream);
 
+/*
+ * truss_decompose_batch -- trussness of every edge of G independent graphs
+ * in one decomposition.  No triangle spans two graphs, so the graphs are
+ * peeled together as one disjoint union (graph g's vertices relabelled to a
+ * contiguous range): one support pass and one level loop (one persistent
+ * launch) serve all of them, and a sub-level of the union is the union of
+ * the graphs' sub-levels at the same level.
+ *   d_src, d_dst : device int32 raw pairs of all graphs; graph g's pairs are
+ *                  [h_eoff[g], h_eoff[g+1]), with vertex ids local to the
+ *                  graph, in [0, h_nverts[g]).
+ *   h_eoff       : host int64[G+1], h_eoff[0] = 0.
+ *   h_nverts     : host int32[G]; their sum must be below 2^31.
+ *   d_truss      : device int32[capacity] (capacity >= total edges; the total
+ *                  number of pairs always suffices): graph after graph, each
+ *                  in its own canonical edge order.
+ *   h_moff       : host int64[G+1] out: graph g's trussness is
+ *                  d_truss[h_moff[g] .. h_moff[g+1]).
+ *   flags, opts, stats: as truss_build_csr / truss_decompose.
+ * Synchronous.  Device workspace is allocated and freed inside the call.
+ */
+TRUSS_API int truss_decompose_batch(const int32_t* d_src, const int32_t* d_dst, const int64_t* h_eoff,
+                                    const int32_t* h_nverts, int32_t G, uint32_t flags, int32_t* d_truss,
+                                    int64_t capacity, int64_t* h_moff, const truss_opts* opts, truss_stats* stats,
+                                    void* stream);
+
 /* Wait for the graph's pending device work on `stream` and return any
  * latched device-side error (and clear it). */
 TRUSS_API int truss_sync(truss_graph* g, void* stream);

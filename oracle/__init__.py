@@ -60,6 +60,8 @@ def bind(path: str):
     lib.or_truss_batch.restype = ctypes.c_int
     lib.or_certify.argtypes = [I32, I64, i32p, i32p, i32p, i32p, ctypes.c_int, i64p]
     lib.or_certify.restype = I64
+    lib.or_certify_sample.argtypes = [I32, I64, i32p, i32p, i32p, i32p, i64p, I64, i64p]
+    lib.or_certify_sample.restype = I64
     return lib
 
 
@@ -214,3 +216,19 @@ def truss_batch(graphs, nthreads: int | None = None):
                             _i32(tau)[1], nthreads)
     _check(rc, "truss_batch")
     return [tau[eoff[i]: eoff[i] + mo[i]].copy() for i in range(G)]
+
+
+def certify_sample(n: int, eu, ev, tau, step, sample):
+    """or_certify's per-edge conditions for the edge ids in ``sample`` and
+    its order check over all edges.  Returns ``(violations, first_bad)``."""
+    lib = _load()
+    eu, up = _i32(eu)
+    ev, vp = _i32(ev)
+    tau, tp = _i32(tau)
+    step, sp = _i32(step)
+    sample = np.ascontiguousarray(sample, np.int64)
+    fb = ctypes.c_int64()
+    r = lib.or_certify_sample(n, eu.shape[0], up, vp, tp, sp, sample.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              sample.shape[0], ctypes.byref(fb))
+    _check(r, "certify_sample")
+    return int(r), int(fb.value)

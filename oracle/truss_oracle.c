@@ -47,6 +47,10 @@
  *                     lie in >= k-2 triangles of later edges while its own
  *                     claim is <= claim(e) < k -- a contradiction.  Edges
  *                     are checked in parallel on host threads.
+ *   or_certify_sample the same per-edge conditions for a sample of edges
+ *                     (rows built only for the sampled edges' endpoints),
+ *                     with the order check over all edges: the check used
+ *                     where the whole certificate costs too long.
  *
  * Readings of the paper taken here (each is stated where it is used):
  *   - the level variable l of Algorithms 4 and 5 is a support value, so
@@ -526,4 +530,88 @@ int64_t or_certify(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, c
     graph_free(&g);
     *first_bad = c.first_bad;
     return bad + (int64_t)atomic_load(&c.violations);
+}
+
+/* ------------------------------------------- sampled result certificate */
+
+/* The per-edge conditions of or_certify for the edges listed in `sample`
+ * only, plus the whole-order monotonicity check and trussness <= support+2
+ * for the sampled edges.  Only the adjacency rows of the sampled edges'
+ * endpoints are built (one pass over all edges), so the cost is O(m) plus
+ * the sampled rows.  Returns the number of violations (0 for an exact
+ * answer; a wrong answer is caught when a sampled edge is wrong or the
+ * order is not monotone), -1 / -2 on bad arguments / allocation failure. */
+int64_t or_certify_sample(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, const int32_t* tau,
+                          const int32_t* step, const int64_t* sample, int64_t ns, int64_t* first_bad) {
+    if (m < 0 || n < 0 || ns < 0 || m > INT32_MAX - 1) return -1;
+    *first_bad = -1;
+    int64_t bad = 0;
+    /* monotone claims along the step order, over all edges */
+    int32_t smax = -1;
+    for (int64_t e = 0; e < m; e++) {
+        if (step[e] < 0 || tau[e] < 2) return -1;
+        if (step[e] > smax) smax = step[e];
+    }
+    int32_t* lo_t = malloc(sizeof(int32_t) * ((size_t)smax + 2));
+    int32_t* hi_t = malloc(sizeof(int32_t) * ((size_t)smax + 2));
+    uint8_t* mark = calloc((size_t)n + 1, 1);
+    int64_t* off = calloc((size_t)n + 2, sizeof(int64_t));
+    if (!lo_t || !hi_t || !mark || !off) { free(lo_t); free(hi_t); free(mark); free(off); return -2; }
+    for (int32_t s = 0; s <= smax; s++) { lo_t[s] = INT32_MAX; hi_t[s] = INT32_MIN; }
+    for (int64_t e = 0; e < m; e++) {
+        if (tau[e] < lo_t[step[e]]) lo_t[step[e]] = tau[e];
+        if (tau[e] > hi_t[step[e]]) hi_t[step[e]] = tau[e];
+    }
+    int32_t run = INT32_MIN;
+    for (int32_t s = 0; s <= smax; s++) {
+        if (lo_t[s] == INT32_MAX) continue;
+        if (lo_t[s] != hi_t[s] || lo_t[s] < run) bad++;
+        run = hi_t[s];
+    }
+    free(lo_t);
+    free(hi_t);
+    /* rows of the sampled endpoints */
+    for (int64_t i = 0; i < ns; i++) {
+        if (sample[i] < 0 || sample[i] >= m) { free(mark); free(off); return -1; }
+        mark[eu[sample[i]]] = 1;
+        mark[ev[sample[i]]] = 1;
+    }
+    for (int64_t e = 0; e < m; e++) {
+        if (mark[eu[e]]) off[eu[e] + 1]++;
+        if (mark[ev[e]]) off[ev[e] + 1]++;
+    }
+    for (int32_t v = 0; v < n; v++) off[v + 1] += off[v];
+    slot_t* adj = malloc(sizeof(slot_t) * (size_t)(off[n] + 1));
+    int64_t* cur = malloc(sizeof(int64_t) * ((size_t)n + 1));
+    if (!adj || !cur) { free(adj); free(cur); free(mark); free(off); return -2; }
+    memcpy(cur, off, sizeof(int64_t) * (size_t)n);
+    for (int64_t e = 0; e < m; e++) {
+        if (mark[eu[e]]) { adj[cur[eu[e]]].w = ev[e]; adj[cur[eu[e]]].e = (int32_t)e; cur[eu[e]]++; }
+        if (mark[ev[e]]) { adj[cur[ev[e]]].w = eu[e]; adj[cur[ev[e]]].e = (int32_t)e; cur[ev[e]]++; }
+    }
+    for (int32_t v = 0; v < n; v++)
+        if (mark[v]) qsort(adj + off[v], (size_t)(off[v + 1] - off[v]), sizeof(slot_t), cmp_slot);
+    /* per sampled edge: merge the two rows */
+    for (int64_t i = 0; i < ns; i++) {
+        const int32_t e = (int32_t)sample[i], u = eu[e], v = ev[e], k = tau[e];
+        int64_t p = off[u], q = off[v], ge = 0, lat = 0, sup = 0;
+        while (p < off[u + 1] && q < off[v + 1]) {
+            if (adj[p].w < adj[q].w) { p++; continue; }
+            if (adj[p].w > adj[q].w) { q++; continue; }
+            const int32_t f = adj[p].e, h = adj[q].e;
+            sup++;
+            if (tau[f] >= k && tau[h] >= k) ge++;
+            if ((step[f] > step[e] || (step[f] == step[e] && f > e)) &&
+                (step[h] > step[e] || (step[h] == step[e] && h > e)))
+                lat++;
+            p++;
+            q++;
+        }
+        if (ge < k - 2 || lat > k - 2 || k > sup + 2) {
+            bad++;
+            if (*first_bad < 0 || e < *first_bad) *first_bad = e;
+        }
+    }
+    free(adj); free(cur); free(mark); free(off);
+    return bad;
 }

@@ -36,6 +36,7 @@ EXPORTS = (
     "truss_strerror", "truss_build_csr", "truss_free", "truss_num_edges", "truss_num_vertices",
     "truss_edge_list", "truss_csr_copy", "truss_support", "truss_default_opts", "truss_decompose",
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
+    "truss_decompose_batch",
 )
 
 
@@ -90,6 +91,8 @@ def _declare(lib):
                                          ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
     lib.truss_sync.argtypes = [vp, vp]
     lib.truss_support_noalloc.argtypes = [vp, vp, vp, i32, i64, vp, vp]
+    lib.truss_decompose_batch.argtypes = [vp, vp, vp, vp, i32, u32, vp, i64, vp, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(Stats), vp]
     for name in EXPORTS:
         if name not in ("truss_strerror", "truss_free", "truss_default_opts"):
             getattr(lib, name).restype = ctypes.c_int
@@ -275,3 +278,31 @@ def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool 
                                      ctypes.byref(m), ctypes.byref(o), ctypes.byref(st), _stream(stream)),
            "truss_decompose_host")
     return out[: m.value], st.as_dict()
+
+
+def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None,
+                    stats: bool = False):
+    """Decompose many independent graphs (objects with ``n``, ``src``,
+    ``dst``; ids local to each graph) in one run on the device.  Returns the
+    list of per-graph trussness arrays (CUDA tensors, canonical order of
+    each graph)."""
+    torch = _torch()
+    G = len(graphs)
+    eoff = np.zeros(G + 1, np.int64)
+    eoff[1:] = np.cumsum([int(g.src.shape[0]) for g in graphs])
+    nverts = np.array([g.n for g in graphs], np.int32)
+    src = torch.from_numpy(np.concatenate([g.src for g in graphs]).astype(np.int32) if G else np.zeros(0, np.int32))
+    dst = torch.from_numpy(np.concatenate([g.dst for g in graphs]).astype(np.int32) if G else np.zeros(0, np.int32))
+    src, dst = src.cuda(), dst.cuda()
+    cap = int(eoff[-1])
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+    moff = np.zeros(G + 1, np.int64)
+    o = default_opts(loop=loop, variant=variant, sync=1)
+    st = Stats()
+    _check(_lib.truss_decompose_batch(_dptr(src) if cap else None, _dptr(dst) if cap else None,
+                                      eoff.ctypes.data_as(ctypes.c_void_p), nverts.ctypes.data_as(ctypes.c_void_p),
+                                      G, (DEGREE_ORDER if degree_order else 0), _dptr(out), cap,
+                                      moff.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), ctypes.byref(st),
+                                      _stream(stream)), "truss_decompose_batch")
+    res = [out[moff[i]: moff[i + 1]] for i in range(G)]
+    return (res, st.as_dict()) if stats else res

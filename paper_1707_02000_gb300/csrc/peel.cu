@@ -388,55 +388,86 @@ __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const 
     }
 }
 
-// Block-wide append (all threads of the block call it together): one
-// atomic per block instead of one per warp.
-__device__ __forceinline__ void block_append(bool pred, int32_t v, int32_t* out, int* count, PeelSmem* sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned b = __ballot_sync(FULL_MASK, pred);
-    if (lane == 0) sm->wcnt[warp] = __popc(b);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int w = 0; w < PW; w++) {
-            const int c = sm->wcnt[w];
-            sm->wcnt[w] = run;
-            run += c;
-        }
-        sm->bbase = run ? atomicAdd(count, run) : 0;
-    }
-    __syncthreads();
-    if (pred) out[sm->bbase + sm->wcnt[warp] + __popc(b & lanemask_lt())] = v;
-    __syncthreads();
-}
 
 // Scan at level l over the live edges: `in` lists them (nullptr: all m
 // edges, in id order).  curr <- {e : S[e] = l}, split into light / heavy
 // lists, their stamps <- g; edges with S > l are the live list of the next
 // Scan (`keep`); cnt.minv <- min(cnt.minv, min{S[e] : S[e] > l}).  Edges
-// below l are processed and drop out for good.
+// below l are processed and drop out for good.  Each thread takes SI
+// consecutive list entries per step (16-byte loads where aligned); the
+// survivors of a whole block step are placed with one block prefix sum and
+// one atomic.
+constexpr int SI = 4;
+
 __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l, int32_t g,
                            const Frontier out, const Slot& cnt, const int32_t* dmin, int hc, uint32_t ocap,
                            PeelSmem* sm) {
     int mn = INT_MAX;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nin; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        int32_t e = 0;
-        int sv = INT_MIN;
-        if (i < nin) {
-            e = in ? __ldcg(in + i) : (int32_t)i;
-            sv = __ldcg(&ss[e].x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * SI;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * SI; base < nin; base += step) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * SI;
+        int32_t e[SI];
+        int sv[SI];
+        if (i0 + SI <= nin) {
+            if (in) {
+                const int4 a = __ldcg(reinterpret_cast<const int4*>(in + i0));
+                e[0] = a.x; e[1] = a.y; e[2] = a.z; e[3] = a.w;
+#pragma unroll
+                for (int k = 0; k < SI; k++) sv[k] = __ldcg(&ss[e[k]].x);
+            } else {
+                const int4* p = reinterpret_cast<const int4*>(ss + i0);
+                const int4 a = __ldcg(p), b = __ldcg(p + 1);
+                sv[0] = a.x; sv[1] = a.z; sv[2] = b.x; sv[3] = b.z;
+#pragma unroll
+                for (int k = 0; k < SI; k++) e[k] = (int32_t)(i0 + k);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < SI; k++) {
+                const bool ok = i0 + k < nin;
+                e[k] = ok ? (in ? __ldcg(in + i0 + k) : (int32_t)(i0 + k)) : 0;
+                sv[k] = ok ? __ldcg(&ss[e[k]].x) : INT_MIN;
+            }
         }
-        const bool hit = sv == l, live = sv > l;
-        if (hit) ss[e].y = g;
-        if (live) mn = min(mn, sv);
-        warp_classify_append(hit, e, dmin, hc, ocap, out, cnt);
-        block_append(live, e, keep, cnt.nlive, sm);
+        int nlive = 0;
+#pragma unroll
+        for (int k = 0; k < SI; k++) {
+            if (sv[k] == l) ss[e[k]].y = g;
+            if (sv[k] > l) {
+                mn = min(mn, sv[k]);
+                nlive++;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SI; k++) warp_classify_append(sv[k] == l, e[k], dmin, hc, ocap, out, cnt);
+        // survivors: block exclusive scan of per-thread counts, one atomic
+        int x = nlive;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm->wcnt[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < PW; w++) {
+                const int c = sm->wcnt[w];
+                sm->wcnt[w] = run;
+                run += c;
+            }
+            sm->bbase = run ? atomicAdd(cnt.nlive, run) : 0;
+        }
+        __syncthreads();
+        int pos = sm->bbase + sm->wcnt[warp] + x - nlive;
+#pragma unroll
+        for (int k = 0; k < SI; k++)
+            if (sv[k] > l) keep[pos++] = e[k];
     }
-    const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
-    if (lane_id() == 0) sm->bmin[warp] = mn;
+    if (lane == 0) sm->bmin[warp] = mn;
     __syncthreads();
     if (threadIdx.x == 0) {
         int b = INT_MAX;

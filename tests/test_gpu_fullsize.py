@@ -58,3 +58,46 @@ def test_rmat10_exact_in_every_form(pkt):
     for loop in (pkt.LOOP_PLAIN, pkt.LOOP_PERSISTENT):
         u, v, tau, step, S, st = _run(pkt, g, loop)
         assert np.array_equal(tau, want)
+
+
+def test_batch_4096_graphs_exact(pkt):
+    """The ragged batch at full size: 4096 Chung-Lu graphs (seeds 1000..5095,
+    log-uniform sizes and mean degrees) in one decomposition, every graph
+    bit-exact against the oracle (Algorithm 1 per graph on host threads)."""
+    gs = gg.chung_lu_batch(4096, seed0=1000)
+    got, st = pkt.decompose_batch(gs, stats=True)
+    want = oracle.truss_batch(gs)
+    assert st["m"] == sum(len(w) for w in want)
+    flat_got = np.concatenate([t.cpu().numpy() for t in got])
+    flat_want = np.concatenate(want)
+    assert np.array_equal(flat_got, flat_want)
+
+
+def test_rmat24_sampled_certificate(pkt):
+    """R-MAT scale 24, edge factor 16 (2^28 samples, int64 row offsets):
+    the edge list is compared in full with the oracle's canonicalisation,
+    the peeling order is checked over all edges, and the per-edge certificate
+    conditions for 20,000 uniformly sampled edges plus the 500 edges of
+    highest trussness and a sample of the last sub-level."""
+    import torch
+
+    g = gg.workload("rmat24_ef16")
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    G = pkt.build_csr(src, dst, g.n, offsets64=True)
+    del src, dst
+    step = torch.empty(G.m, dtype=torch.int32, device="cuda")
+    tau = G.decompose(loop=pkt.LOOP_PERSISTENT, peel_step=step).cpu().numpy()
+    step = step.cpu().numpy()
+    u, v = G.edge_list()
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    G.free()
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    assert np.array_equal(u, eu) and np.array_equal(v, ev)
+    rng = np.random.default_rng(24)
+    top = np.argsort(tau)[-500:]
+    last = np.nonzero(step == step.max())[0]
+    sample = np.unique(np.concatenate([rng.choice(eu.size, 20000, replace=False), top,
+                                       rng.choice(last, min(200, last.size), replace=False)]))
+    bad, first = oracle.certify_sample(g.n, eu, ev, tau, step, sample)
+    assert bad == 0, f"{bad} violations (first edge {first})"

@@ -356,3 +356,25 @@ def test_sublevel_trace(pkt, loop):
         sel = step == k
         assert tr["dsum"][k] == int(dmin[sel].sum()) and tr["dmax"][k] == int(dmin[sel].max())
         assert tr["n_light"][k] == int((dmin[sel] <= 32).sum())
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_batch_matches_oracle(pkt, loop):
+    """Many independent graphs of uneven size in one run (their disjoint
+    union), including an empty graph and a triangle-free one."""
+    gs = gg.chung_lu_batch(48, seed0=1000)
+    gs.insert(5, gg.EdgeList(7, np.zeros(0, np.int32), np.zeros(0, np.int32), "empty"))
+    gs.insert(9, gg.EdgeList(6, np.arange(5, dtype=np.int32), np.arange(1, 6, dtype=np.int32), "path"))
+    got = pkt.decompose_batch(gs, loop=_loop(pkt, loop))
+    want = oracle.truss_batch(gs, nthreads=4)
+    assert len(got) == len(gs)
+    for g, t, w in zip(gs, got, want):
+        assert np.array_equal(host(t), w), g.name
+
+
+def test_batch_rejects_ids_outside_their_graph(pkt):
+    a = gg.EdgeList(3, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    b = gg.EdgeList(3, np.array([0, 1], np.int32), np.array([1, 3], np.int32))  # 3 is outside graph b
+    with pytest.raises(pkt.TrussError) as ex:
+        pkt.decompose_batch([a, b])
+    assert ex.value.status == pkt.EBADGRAPH

@@ -338,3 +338,27 @@ def test_certificate_rejects_wrong_answers():
     assert oracle.certify(g.n, eu, ev, tau, s2)[0] > 0
     # all claims 2 (a valid lower bound, but no valid order)
     assert oracle.certify(g.n, eu, ev, np.full_like(tau, 2), step)[0] > 0
+
+
+def test_sampled_certificate():
+    """The sampled certificate agrees with the full one: it accepts the exact
+    answer for any sample, and flags a perturbed edge whenever that edge is
+    sampled (and an order violation whatever the sample)."""
+    g = gg.chung_lu(3000, 2.1, 14.0, 300.0, seed=8)
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    tau, lv, sz, step = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+    rng = np.random.default_rng(3)
+    sample = rng.choice(eu.size, 500, replace=False)
+    assert oracle.certify_sample(g.n, eu, ev, tau, step, sample) == (0, -1)
+    assert oracle.certify_sample(g.n, eu, ev, tau, step, np.arange(eu.size))[0] == 0
+    for e in sample[:20]:
+        for d in (-1, 1):
+            t2 = tau.copy()
+            t2[e] += d
+            if t2[e] < 2:
+                continue
+            bad, first = oracle.certify_sample(g.n, eu, ev, t2, step, sample)
+            assert bad > 0
+    s2 = step.copy()
+    s2[np.argmax(tau)] = 0
+    assert oracle.certify_sample(g.n, eu, ev, tau, s2, sample[:10])[0] > 0
