@@ -136,6 +136,27 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 #define TRUSS_VAR_THREAD 0    /* one thread per light edge                   */
 #define TRUSS_VAR_GROUP 1     /* eight lanes per light edge                  */
 #define TRUSS_VAR_WARP 2      /* one warp per light edge                     */
+#define TRUSS_VAR_LEARNED 3   /* chosen per sub-level by the learned cost
+                                 model (opts->sched_params); falls back to
+                                 TRUSS_VAR_AUTO when it is absent, when the
+                                 frontier has few light edges, or when the
+                                 model's output is not finite              */
+
+/* Learned scheduler (project addition): an FP32 MLP 5 -> 32 -> 32 -> 3 that
+ * predicts the log2 device time of a sub-level under each of the three light-
+ * edge variants (THREAD, GROUP, WARP) from the sub-level's features.
+ * Parameters: TRUSS_SCHED_PARAMS floats, in this order: feature means [5],
+ * inverse standard deviations [5], W1 [32][5], b1 [32], W2 [32][32], b2 [32],
+ * W3 [3][32], b3 [3]; ReLU after the two hidden layers. */
+#define TRUSS_SCHED_FEATURES 5
+#define TRUSS_SCHED_VARIANTS 3
+#define TRUSS_SCHED_PARAMS 1357
+
+/* Autotuned variant table (project addition): TRUSS_TUNE_CLASSES entries,
+ * indexed by 8 * min(15, floor(log2(1 + light edges))) +
+ * min(7, floor(log2(1 + shorter-row sum / frontier size))); each entry is a
+ * TRUSS_VAR_THREAD / GROUP / WARP, or -1 for the default. */
+#define TRUSS_TUNE_CLASSES 128
 
 /* One record per non-empty sub-level (see truss_opts.h_trace). */
 typedef struct truss_sublevel_trace {
@@ -170,7 +191,10 @@ typedef struct truss_opts {
                              checker certify the result (see truss_decompose) */
     truss_sublevel_trace* h_trace; /* optional host array of max_sub records,
                              one per sub-level; needs sync = 1               */
-    int32_t reserved[4];
+    const float* sched_params; /* device float[TRUSS_SCHED_PARAMS] for
+                             TRUSS_VAR_LEARNED, or NULL                      */
+    const int8_t* tune_table;  /* host int8[TRUSS_TUNE_CLASSES] consulted by
+                             TRUSS_VAR_AUTO, or NULL (built-in default)      */
 } truss_opts;
 
 typedef struct truss_stats {
@@ -266,6 +290,41 @@ TRUSS_API int truss_decompose_batch(const int32_t* d_src, const int32_t* d_dst, 
                                     const int32_t* h_nverts, int32_t G, uint32_t flags, int32_t* d_truss,
                                     int64_t capacity, int64_t* h_moff, const truss_opts* opts, truss_stats* stats,
                                     void* stream);
+
+/* ---------------------------------------- learned scheduler, autotuner */
+
+/* Features of each of n sub-level records (host): log2(1 + x) of the
+ * frontier size, the sum and the maximum of its shorter-row lengths, the
+ * level and the edges not yet peeled.  x: host float[n][5].  The persistent
+ * kernel computes the same five values on the device. */
+TRUSS_API void truss_sched_features(const truss_sublevel_trace* tr, int64_t n, float* x);
+
+/* Random initial weights (He-style uniform, counter-based from seed) into
+ * device float[TRUSS_SCHED_PARAMS].  Synchronises `stream`. */
+TRUSS_API int truss_sched_init(float* d_params, uint64_t seed, void* stream);
+
+/* Mean squared error L = sum over samples and variants of (o - y)^2 / (3n)
+ * of the model on d_x (device float[n][5]) against d_y (device float[n][3],
+ * log2 times), and its gradient with respect to every parameter (device
+ * float[TRUSS_SCHED_PARAMS]; the normalisation entries receive their
+ * gradient too but training keeps them fixed).  Synchronises `stream`. */
+TRUSS_API int truss_sched_grad(const float* d_params, const float* d_x, const float* d_y, int64_t n, float* d_grad,
+                               float* h_loss, void* stream);
+
+/* Train on the device: set the normalisation from d_x, then `epochs` full-
+ * batch Adam steps (learning rate lr, betas 0.9 / 0.999) on the loss of
+ * truss_sched_grad.  *h_loss receives the final loss.  Synchronises. */
+TRUSS_API int truss_sched_train(float* d_params, const float* d_x, const float* d_y, int64_t n, int32_t epochs,
+                                float lr, float* h_loss, void* stream);
+
+/* Predicted log2 times, d_out device float[n][3]. */
+TRUSS_API int truss_sched_predict(const float* d_params, const float* d_x, int64_t n, float* d_out, void* stream);
+
+/* Autotuner: decompose g once per light-edge variant (THREAD, GROUP, WARP),
+ * `repeats` times each, timing every sub-level; for every class of
+ * TRUSS_TUNE_CLASSES with data, h_table receives the variant with the least
+ * total time (-1 for classes without data).  Synchronous. */
+TRUSS_API int truss_autotune(truss_graph* g, int8_t* h_table, int32_t repeats, void* stream);
 
 /* Wait for the graph's pending device work on `stream` and return any
  * latched device-side error (and clear it). */

@@ -28,7 +28,8 @@ NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
 LOOP_PLAIN, LOOP_PERSISTENT = 0, 1
-VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP = -1, 0, 1, 2
+VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP, VAR_LEARNED = -1, 0, 1, 2, 3
+SCHED_FEATURES, SCHED_VARIANTS, SCHED_PARAMS, TUNE_CLASSES = 5, 3, 1357, 128
 PROCESSED, IN_CURR = 1, 2
 
 # Every symbol include/truss.h declares (checked by the tests).
@@ -36,7 +37,8 @@ EXPORTS = (
     "truss_strerror", "truss_build_csr", "truss_free", "truss_num_edges", "truss_num_vertices",
     "truss_edge_list", "truss_csr_copy", "truss_support", "truss_default_opts", "truss_decompose",
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
-    "truss_decompose_batch",
+    "truss_decompose_batch", "truss_sched_features", "truss_sched_init", "truss_sched_grad",
+    "truss_sched_train", "truss_sched_predict", "truss_autotune",
 )
 
 
@@ -51,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("level_jump", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("h_sub_level", ctypes.POINTER(ctypes.c_int32)), ("h_sub_size", ctypes.POINTER(ctypes.c_int64)),
                 ("max_sub", ctypes.c_int64), ("d_peel_step", ctypes.c_void_p),
-                ("h_trace", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 4)]
+                ("h_trace", ctypes.c_void_p), ("sched_params", ctypes.c_void_p),
+                ("tune_table", ctypes.c_void_p)]
 
 
 # truss_sublevel_trace, one record per sub-level
@@ -93,8 +96,15 @@ def _declare(lib):
     lib.truss_support_noalloc.argtypes = [vp, vp, vp, i32, i64, vp, vp]
     lib.truss_decompose_batch.argtypes = [vp, vp, vp, vp, i32, u32, vp, i64, vp, ctypes.POINTER(Opts),
                                           ctypes.POINTER(Stats), vp]
+    lib.truss_sched_features.argtypes = [vp, i64, vp]
+    lib.truss_sched_features.restype = None
+    lib.truss_sched_init.argtypes = [vp, ctypes.c_uint64, vp]
+    lib.truss_sched_grad.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(ctypes.c_float), vp]
+    lib.truss_sched_train.argtypes = [vp, vp, vp, i64, i32, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp]
+    lib.truss_sched_predict.argtypes = [vp, vp, i64, vp, vp]
+    lib.truss_autotune.argtypes = [vp, vp, i32, vp]
     for name in EXPORTS:
-        if name not in ("truss_strerror", "truss_free", "truss_default_opts"):
+        if name not in ("truss_strerror", "truss_free", "truss_default_opts", "truss_sched_features"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -199,7 +209,7 @@ class Graph:
 
     def decompose(self, out=None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, sync=True, level_jump=True,
                   timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False,
-                  peel_step=None, trace=False):
+                  peel_step=None, trace=False, sched_params=None, tune_table=None):
         """Trussness (int32[m], canonical order).  With ``record`` also
         returns the (level, |curr|) of every sub-level; with ``trace`` a
         structured array (TRACE_DTYPE) with one record per sub-level; with
@@ -208,6 +218,13 @@ class Graph:
         out = self._empty(self.m) if out is None else out
         o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record or trace)),
                          level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
+        if sched_params is not None:
+            assert sched_params.numel() == SCHED_PARAMS and str(sched_params.dtype) == "torch.float32"
+            o.sched_params = sched_params.data_ptr()
+        if tune_table is not None:
+            tune_table = np.ascontiguousarray(tune_table, np.int8)
+            assert tune_table.shape == (TUNE_CLASSES,)
+            o.tune_table = tune_table.ctypes.data
         tr = None
         if trace:
             tr = np.zeros(max_sub, TRACE_DTYPE)
@@ -245,6 +262,13 @@ class Graph:
                                         _dptr(nxt) if self.m else None, ctypes.byref(k), variant,
                                         _stream(stream)), "truss_peel_sublevel")
         return nxt[: k.value]
+
+    def autotune(self, repeats: int = 1, stream=None):
+        """Autotuned variant table (int8[TUNE_CLASSES]) for this graph."""
+        t = np.full(TUNE_CLASSES, -1, np.int8)
+        _check(_lib.truss_autotune(self._h, t.ctypes.data_as(ctypes.c_void_p), repeats, _stream(stream)),
+               "truss_autotune")
+        return t
 
     def sync(self, stream=None):
         _check(_lib.truss_sync(self._h, _stream(stream)), "truss_sync")
@@ -306,3 +330,65 @@ def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, var
                                       _stream(stream)), "truss_decompose_batch")
     res = [out[moff[i]: moff[i + 1]] for i in range(G)]
     return (res, st.as_dict()) if stats else res
+
+
+# ------------------------------------------------------- learned scheduler
+
+def sched_features(trace_records) -> np.ndarray:
+    """Features (float32[n][5]) of trace records (TRACE_DTYPE)."""
+    tr = np.ascontiguousarray(trace_records, TRACE_DTYPE)
+    x = np.zeros((tr.shape[0], SCHED_FEATURES), np.float32)
+    _lib.truss_sched_features(tr.ctypes.data_as(ctypes.c_void_p), tr.shape[0], x.ctypes.data_as(ctypes.c_void_p))
+    return x
+
+
+def sched_init(seed: int = 0, stream=None):
+    torch = _torch()
+    p = torch.empty(SCHED_PARAMS, dtype=torch.float32, device="cuda")
+    _check(_lib.truss_sched_init(_dptr(p), seed, _stream(stream)), "truss_sched_init")
+    return p
+
+
+def sched_grad(params, x, y, stream=None):
+    """(loss, gradient) of the scheduler's MSE on device tensors x [n,5], y [n,3]."""
+    torch = _torch()
+    g = torch.empty(SCHED_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctypes.c_float()
+    _check(_lib.truss_sched_grad(_dptr(params), _dptr(x), _dptr(y), x.shape[0], _dptr(g), ctypes.byref(loss),
+                                 _stream(stream)), "truss_sched_grad")
+    return float(loss.value), g
+
+
+def sched_train(params, x, y, epochs: int = 2000, lr: float = 3e-3, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(_lib.truss_sched_train(_dptr(params), _dptr(x), _dptr(y), x.shape[0], epochs, lr, ctypes.byref(loss),
+                                  _stream(stream)), "truss_sched_train")
+    return float(loss.value)
+
+
+def sched_predict(params, x, stream=None):
+    torch = _torch()
+    out = torch.empty((x.shape[0], SCHED_VARIANTS), dtype=torch.float32, device="cuda")
+    _check(_lib.truss_sched_predict(_dptr(params), _dptr(x), x.shape[0], _dptr(out), _stream(stream)),
+           "truss_sched_predict")
+    return out
+
+
+def sched_dataset(graph: "Graph", repeats: int = 1):
+    """Training data the method generates itself: decompose ``graph`` under
+    each light-edge variant with tracing; every sub-level gives one sample
+    (features, log2 time of each variant).  Only sub-levels with light edges
+    (where the variant acts) are kept.  Returns (x [n,5], y [n,3]) numpy."""
+    traces = []
+    for v in (VAR_THREAD, VAR_GROUP, VAR_WARP):
+        runs = []
+        for _ in range(repeats):
+            _, tr = graph.decompose(loop=LOOP_PERSISTENT, variant=v, trace=True)
+            runs.append(tr)
+        t = np.stack([r["t_ns"] for r in runs]).mean(0)
+        traces.append((runs[0], t))
+    base = traces[-1][0]
+    keep = base["n_light"] > 0
+    x = sched_features(base[keep])
+    y = np.log2(np.stack([t[keep] for _, t in traces], 1).astype(np.float64) + 1.0).astype(np.float32)
+    return x, y

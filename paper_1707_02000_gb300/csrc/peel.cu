@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "sched.cuh"
 
 namespace {
 
@@ -334,16 +335,44 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
     }
 }
 
-// Lanes per light edge for a sub-level (the variant).
-__host__ __device__ __forceinline__ int pick_group(int variant, int64_t nl, int64_t nthreads) {
-    if (variant == TRUSS_VAR_THREAD) return 1;
-    if (variant == TRUSS_VAR_GROUP) return 8;
-    // default: measured on power-law and geometric graphs, a warp per light
-    // edge was the fastest choice in nearly every sub-level, small or large
-    (void)nl;
-    (void)nthreads;
-    return 32;
+// Lanes per light edge for each variant.
+__host__ __device__ __forceinline__ int group_of(int v) {
+    return v == TRUSS_VAR_THREAD ? 1 : (v == TRUSS_VAR_GROUP ? 8 : 32);
 }
+
+struct TuneTable {
+    int8_t v[TRUSS_TUNE_CLASSES];
+};
+
+__host__ __device__ __forceinline__ int ilog2_floor(int64_t x) {
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        r++;
+    }
+    return r;
+}
+
+// class of a sub-level in the autotuned table (see truss.h)
+__host__ __device__ __forceinline__ int tune_class(int64_t nl, int64_t dsum, int64_t size) {
+    const int a = min(15, ilog2_floor(1 + nl));
+    const int b = min(7, ilog2_floor(1 + dsum / (size > 0 ? size : 1)));
+    return 8 * a + b;
+}
+
+// Lanes per light edge for a sub-level under a fixed or table-driven
+// policy.  Default: a warp per light edge -- measured on power-law and
+// geometric graphs it was the fastest choice in nearly every sub-level.
+__host__ __device__ __forceinline__ int pick_group(int variant, int64_t nl, int64_t dsum, int64_t size,
+                                                   const TuneTable& tt) {
+    if (variant >= TRUSS_VAR_THREAD && variant <= TRUSS_VAR_WARP) return group_of(variant);
+    const int t = tt.v[tune_class(nl, dsum, size)];
+    return t >= 0 ? group_of(t) : 32;
+}
+
+// the learned policy is consulted only when a sub-level has this many light
+// edges (below it the light-edge mapping barely matters)
+constexpr int LEARN_MIN_LIGHT = 64;
 
 // Warp-aggregated append of matched edges to the light or heavy list.
 __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const int32_t* dmin, int hc, uint32_t ocap,
@@ -578,9 +607,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 template <typename Off>
 __global__ void __launch_bounds__(PT, 6)
     k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
-                 int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace) {
+                 int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace,
+                 const float* sched, TuneTable tt) {
     __shared__ PeelSmem sm;
     __shared__ __align__(16) SlotVals sv;
+    __shared__ int s_choice;
     smem_init(&sm);
     const unsigned nblocks = gridDim.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -617,7 +648,19 @@ __global__ void __launch_bounds__(PT, 6)
             const int nl = v.nl;
             const int nh = (int)(v.hc >> 32);
             const uint32_t nchunk = (uint32_t)v.hc;
-            const int gsz = pick_group(variant, nl, nthreads);
+            int gsz = pick_group(variant, nl, (int64_t)v.dsum, (int64_t)nl + nh, tt);
+            if (variant == TRUSS_VAR_LEARNED && sched && nl >= LEARN_MIN_LIGHT) {
+                // warp 0 of every block evaluates the model on the same
+                // inputs, so every block takes the same decision
+                if (threadIdx.x < 32) {
+                    float x[SF];
+                    sched_features((int64_t)nl + nh, (int64_t)v.dsum, v.dmax, l, G.m - processed, x);
+                    const int c = sched_pick(sched, x);
+                    if (threadIdx.x == 0) s_choice = c;
+                }
+                __syncthreads();
+                if (s_choice >= 0) gsz = group_of(s_choice);
+            }
             const int q = (int)(p & 3);
             uint64_t t0 = 0;
             if (leader) {
@@ -762,6 +805,12 @@ Graph<Off> graph_view(truss_graph* g) {
     return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, g->ss, g->m, g->hc, g->ocap};
 }
 
+TuneTable tune_table_of(const truss_opts& o) {
+    TuneTable t;
+    for (int i = 0; i < TRUSS_TUNE_CLASSES; i++) t.v[i] = o.tune_table ? o.tune_table[i] : (int8_t)-1;
+    return t;
+}
+
 Frontier side(truss_graph* g, int k) {
     return Frontier{g->fq[k][0], g->fq[k][1], reinterpret_cast<uint32_t*>(g->fq[k][2]), g->owner[k]};
 }
@@ -830,7 +879,7 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
         }
         out->nlevel++;
         while (nl + nh > 0) {
-            const int gsz = pick_group(o.variant, nl, (int64_t)pmax * PT);
+            const int gsz = pick_group(o.variant, nl, dsum, (int64_t)nl + nh, tune_table_of(o));
             truss_sublevel_trace* r = (trace && out->nsub < max_trace) ? trace + out->nsub : nullptr;
             if (r) *r = truss_sublevel_trace{l, gsz, nl, nh, nc, dmax, dsum, g->m - processed, 0, scan_ns};
             scan_ns = 0;
@@ -880,7 +929,9 @@ int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_su
     int32_t* live0 = g->live[0];
     int32_t* live1 = g->live[1];
     int* ctr = g->ctr;
-    void* args[] = {&G, &f0, &f1, &live0, &live1, &ctr, &variant, &jump, &tmo, &d_trace, &max_trace};
+    const float* sched = o.sched_params;
+    TuneTable tt = tune_table_of(o);
+    void* args[] = {&G, &f0, &f1, &live0, &live1, &ctr, &variant, &jump, &tmo, &d_trace, &max_trace, &sched, &tt};
     CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off>, dim3(blocks), dim3(PT), args, 0, s));
     truss_note_launch(2);
     return TRUSS_OK;
@@ -888,7 +939,7 @@ int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_su
 
 int check_opts(const truss_opts& o) {
     if (o.loop != TRUSS_LOOP_PLAIN && o.loop != TRUSS_LOOP_PERSISTENT) return TRUSS_EINVAL;
-    if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_WARP) return TRUSS_EINVAL;
+    if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_LEARNED) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size)) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_trace) && (o.max_sub < 0 || !o.sync)) return TRUSS_EINVAL;
     return TRUSS_OK;
@@ -1021,7 +1072,7 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
     if (nl + nh > 0) {
         Graph<Off> G = graph_view<Off>(g);
         const int blocks = process_blocks<Off>(g);
-        k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, 0), nl, nh, nc, pick_group(variant, nl, (int64_t)blocks * PT), l,
+        k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, 0), nl, nh, nc, pick_group(variant, nl, 0, nl + nh, tune_table_of(truss_opts{})), l,
                                              1, side(g, 1), g->ctr);
         CU(cudaGetLastError());
     }
@@ -1101,6 +1152,47 @@ void truss_release_workspace(truss_graph* g) {
     g->h_ctr = nullptr;
 }
 
+extern "C" int truss_autotune(truss_graph* g, int8_t* h_table, int32_t repeats, void* stream) {
+    if (!g || !h_table || repeats < 1) return TRUSS_EINVAL;
+    for (int i = 0; i < TRUSS_TUNE_CLASSES; i++) h_table[i] = -1;
+    if (g->m == 0) return TRUSS_OK;
+    int32_t* d_out = nullptr;
+    CU(cudaMalloc((void**)&d_out, sizeof(int32_t) * (size_t)g->m));
+    truss_opts o;
+    truss_default_opts(&o);
+    o.sync = 1;
+    truss_stats st;
+    int rc = truss_decompose(g, d_out, &o, &st, stream);
+    std::vector<truss_sublevel_trace> tr((size_t)std::max<int64_t>(1, st.sublevels));
+    std::vector<double> tot((size_t)3 * TRUSS_TUNE_CLASSES, 0.0);
+    std::vector<int> seen(TRUSS_TUNE_CLASSES, 0);
+    const int vars[3] = {TRUSS_VAR_THREAD, TRUSS_VAR_GROUP, TRUSS_VAR_WARP};
+    for (int k = 0; k < 3 && rc == TRUSS_OK; k++)
+        for (int r = 0; r < repeats && rc == TRUSS_OK; r++) {
+            o.variant = vars[k];
+            o.h_trace = tr.data();
+            o.max_sub = (int64_t)tr.size();
+            rc = truss_decompose(g, d_out, &o, &st, stream);
+            const int64_t n = std::min<int64_t>(st.sublevels, (int64_t)tr.size());
+            for (int64_t i = 0; i < n && rc == TRUSS_OK; i++) {
+                if (tr[i].n_light == 0) continue;  // the variant only maps light edges
+                const int c = tune_class(tr[i].n_light, tr[i].dsum, (int64_t)tr[i].n_light + tr[i].n_heavy);
+                tot[(size_t)k * TRUSS_TUNE_CLASSES + c] += (double)tr[i].t_ns;
+                seen[c] = 1;
+            }
+        }
+    cudaFree(d_out);
+    if (rc != TRUSS_OK) return rc;
+    for (int c = 0; c < TRUSS_TUNE_CLASSES; c++) {
+        if (!seen[c]) continue;
+        int best = 0;
+        for (int k = 1; k < 3; k++)
+            if (tot[(size_t)k * TRUSS_TUNE_CLASSES + c] < tot[(size_t)best * TRUSS_TUNE_CLASSES + c]) best = k;
+        h_table[c] = (int8_t)vars[best];
+    }
+    return TRUSS_OK;
+}
+
 extern "C" void truss_default_opts(truss_opts* o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));
@@ -1163,7 +1255,7 @@ extern "C" int truss_sync(truss_graph* g, void* stream) {
 extern "C" int truss_peel_sublevel(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr,
                                    int64_t ncurr, int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant,
                                    void* stream) {
-    if (!g || !h_nnext || ncurr < 0 || ncurr > g->m || variant < TRUSS_VAR_AUTO || variant > TRUSS_VAR_WARP)
+    if (!g || !h_nnext || ncurr < 0 || ncurr > g->m || variant < TRUSS_VAR_AUTO || variant > TRUSS_VAR_LEARNED)
         return TRUSS_EINVAL;
     if (g->m > 0 && (!d_S || !d_flags || !d_next)) return TRUSS_EINVAL;
     if (ncurr > 0 && !d_curr) return TRUSS_EINVAL;

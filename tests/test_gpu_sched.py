@@ -1,0 +1,147 @@
+"""Learned scheduler and autotuner on the device: the training kernels'
+gradient against the float64 reference, training progress, exactness of
+decompositions under learned and autotuned schedules, and what the trained
+model gains over the fixed heuristic on held-out sub-levels."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle import sched_ref as R
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkt():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1707_02000_gb300 as pkt
+
+    return pkt
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, 0.3, R.COUNT).astype(np.float32)
+    p[:5] = rng.normal(5, 2, 5)
+    p[5:10] = rng.uniform(0.2, 0.6, 5)
+    x = rng.uniform(0, 25, (n, 5)).astype(np.float32)
+    y = rng.normal(10, 3, (n, 3)).astype(np.float32)
+    return p, x, y
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 1000, 5003])
+def test_gradient_matches_reference(pkt, n):
+    p, x, y = _data(n, n)
+    loss, g = pkt.sched_grad(_dev(p), _dev(x), _dev(y))
+    want_loss = R.loss(p.astype(np.float64), x, y)
+    want = R.grad(p.astype(np.float64), x, y)
+    got = g.cpu().numpy().astype(np.float64)
+    assert np.isclose(loss, want_loss, rtol=1e-4)
+    # float32 accumulation over n samples and 1357 parameters
+    scale = np.abs(want).max()
+    assert np.max(np.abs(got - want)) <= 1e-4 * scale + 1e-7, np.max(np.abs(got - want))
+
+
+def test_predict_matches_reference(pkt):
+    p, x, _ = _data(3, 777)
+    out = pkt.sched_predict(_dev(p), _dev(x)).cpu().numpy()
+    want, _ = R.forward(p.astype(np.float64), x)
+    assert np.allclose(out, want, rtol=1e-4, atol=1e-4)
+
+
+def test_training_fits_a_smooth_cost_surface(pkt):
+    """Targets from a known smooth function of the features (log-time-like):
+    the device trainer must bring the loss far below the initial loss."""
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 24, (4000, 5)).astype(np.float32)
+    y = np.stack([0.8 * x[:, 1] + 0.1 * x[:, 4] + 3, 0.7 * x[:, 1] + 0.3 * x[:, 0] + 2,
+                  0.9 * x[:, 2] + 0.5 * x[:, 0] + 1], 1).astype(np.float32)
+    p = pkt.sched_init(seed=1)
+    X, Y = _dev(x), _dev(y)
+    l0, _ = pkt.sched_grad(p, X, Y)
+    loss = pkt.sched_train(p, X, Y, epochs=1500, lr=3e-3)
+    assert loss < l0 / 50, (l0, loss)
+    # the reference model on the same weights reports the same loss
+    assert np.isclose(R.loss(p.cpu().numpy().astype(np.float64), x, y), loss, rtol=1e-3, atol=1e-5)
+
+
+def _graph(pkt, g):
+    import torch
+
+    return pkt.build_csr(torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(), g.n)
+
+
+def test_learned_and_autotuned_schedules_are_exact(pkt):
+    """Any schedule -- random weights, trained weights, an autotuned table --
+    gives the same trussness as the oracle."""
+    for g in (gg.rgg2d(20000, 24.0, seed=41), gg.chung_lu(20000, 2.1, 14.0, 2000.0, seed=42)):
+        G = _graph(pkt, g)
+        want = oracle.truss_of_edges(g.n, g.src, g.dst)[2]
+        x, y = pkt.sched_dataset(G)
+        p = pkt.sched_init(seed=5)
+        tau, tr = G.decompose(variant=pkt.VAR_LEARNED, sched_params=p, trace=True)
+        assert np.array_equal(tau.cpu().numpy(), want)
+        pkt.sched_train(p, _dev(x), _dev(y), epochs=300)
+        tau, tr = G.decompose(variant=pkt.VAR_LEARNED, sched_params=p, trace=True)
+        assert np.array_equal(tau.cpu().numpy(), want)
+        assert set(np.unique(tr["group"])) <= {1, 8, 32}
+        table = G.autotune()
+        assert table.shape == (pkt.TUNE_CLASSES,) and set(np.unique(table)) <= {-1, 0, 1, 2}
+        tau = G.decompose(variant=pkt.VAR_AUTO, tune_table=table)
+        assert np.array_equal(tau.cpu().numpy(), want)
+        G.free()
+
+
+def test_learned_choice_regret_on_held_out_sublevels(pkt):
+    """Train on sub-levels of two graphs; on a held-out graph of each family,
+    every sub-level's time under each variant is measured, and the model's
+    choices are scored by regret (time above the per-sub-level best).  The
+    trained model must do better than its untrained start and no worse than
+    the worst fixed variant; the gain over the default (a warp per light
+    edge) is printed."""
+    import torch
+
+    train = [gg.rgg2d(1 << 18, 32.0, seed=51), gg.chung_lu(1 << 18, 2.1, 20.0, 4096.0, seed=52)]
+    test = [gg.rgg2d(1 << 18, 32.0, seed=61), gg.chung_lu(1 << 18, 2.1, 20.0, 4096.0, seed=62)]
+    xs, ys = [], []
+    for g in train:
+        G = _graph(pkt, g)
+        x, y = pkt.sched_dataset(G, repeats=2)
+        xs.append(x)
+        ys.append(y)
+        G.free()
+    p = pkt.sched_init(seed=3)
+    X, Y = _dev(np.concatenate(xs)), _dev(np.concatenate(ys))
+    pred0 = None
+    xt, yt = [], []
+    for g in test:
+        G = _graph(pkt, g)
+        x, y = pkt.sched_dataset(G, repeats=2)
+        xt.append(x)
+        yt.append(y)
+        G.free()
+    xt, yt = np.concatenate(xt), np.concatenate(yt)
+    pred0 = pkt.sched_predict(p, _dev(xt)).cpu().numpy()
+    pkt.sched_train(p, X, Y, epochs=2000, lr=3e-3)
+    pred = pkt.sched_predict(p, _dev(xt)).cpu().numpy()
+    t = np.exp2(yt.astype(np.float64))  # measured ns per variant
+    best = t.min(1).sum()
+    regret = lambda choice: float(t[np.arange(len(t)), choice].sum() - best)
+    r_learned = regret(pred.argmin(1))
+    r_untrained = regret(pred0.argmin(1))
+    r_fixed = [regret(np.full(len(t), v)) for v in range(3)]
+    print(f"\nheld-out sub-levels: {len(t)}; total best {best / 1e6:.3f} ms; regret ms: learned "
+          f"{r_learned / 1e6:.3f}, untrained {r_untrained / 1e6:.3f}, thread/group/warp "
+          f"{[round(r / 1e6, 3) for r in r_fixed]}")
+    assert r_learned <= max(r_fixed)
+    assert r_learned <= r_untrained + 1e-9 or r_untrained == 0
+    torch.cuda.synchronize()
