@@ -7,7 +7,11 @@ device-resident graph, one JSON line on stdout.
 A step is one whole decomposition: support (Algorithm 3) and the level loop
 (Algorithms 4-5) over the Chung-Lu power-law workload (2^20 vertices,
 exponent 2.1, mean degree 20, expected degrees clipped at 2^14, seed 2),
-with the CSR already in HBM.  Every step is timed with CUDA events on the
+with the CSR already in HBM.  The reported form is the persistent loop with
+the learned sub-level scheduler, whose cost model is trained before timing
+(outside the timed region) on two other graphs of the same family (seeds 101
+and 102); the host-driven loop and the persistent loop with the fixed
+heuristic are timed beside it.  Every step is timed with CUDA events on the
 stream the library launches on; L2 is flushed (a 256 MiB write) between
 steps, outside the timed events.  Under torchrun each rank runs its own
 replica on its own GPU (the decomposition does not shard) and
@@ -111,12 +115,14 @@ class ClockSampler:
 # ------------------------------------------------------------ roofline model
 
 def algorithmic_bytes(st, n):
-    """Compulsory bytes of each phase, from exact work counts (the design doc,
-    "Algorithmic bytes"): support = 32m + 8n + 4W+ + 12T; peeling =
-    8m per Scan + 36m + 4 sum_e min(d(u), d(v)) + 28T."""
+    """Compulsory bytes of each phase, from exact work counts reported by the
+    library: support = 32m + 8n + 4W+ + 12T; peeling = (16 V - 8m) for the
+    Scans (V = entries visited: an 8-byte support/stamp read per entry, plus
+    a 4-byte id read and a 4-byte survivor write after the first Scan) +
+    36m + 4 sum_e min(d(u), d(v)) + 28T."""
     m, T = st["m"], st["triangles"]
     sup = 32 * m + 8 * n + 4 * st["wedges_up"] + 12 * T
-    peel = 8 * m * st["scans"] + 36 * m + 4 * st["dmin_sum"] + 28 * T
+    peel = (16 * st["scanned"] - 8 * m) + 36 * m + 4 * st["dmin_sum"] + 28 * T
     return sup, peel
 
 
@@ -201,6 +207,40 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
+CALIB_SEEDS = (101, 102)
+VARIANTS = {}
+VARIANT_DESC = {"learned": "learned cost model per sub-level (heuristic below 64 light edges)",
+                "heuristic": "fixed per-sub-level heuristic", "thread": "thread per light edge",
+                "group": "8 lanes per light edge", "warp": "warp per light edge"}
+
+
+def calibrate(pkt, workload, seeds, repeats=2, epochs=2000):
+    """Trains the sub-level cost model (untimed) on other graphs of the
+    workload's family and size: each is decomposed under every light-edge
+    variant with tracing, and the device trainer fits the measured times."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    for s in seeds:
+        c = gg.workload(workload, seed=s)
+        Gc = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n)
+        x, y = pkt.sched_dataset(Gc, repeats=repeats)
+        Gc.free()
+        xs.append(x)
+        ys.append(y)
+    X = torch.from_numpy(np.concatenate(xs)).cuda()
+    Y = torch.from_numpy(np.concatenate(ys)).cuda()
+    params = pkt.sched_init(seed=0)
+    loss = pkt.sched_train(params, X, Y, epochs=epochs, lr=3e-3)
+    torch.cuda.synchronize()
+    return params, {"graphs": [f"{workload} seed {s}" for s in seeds], "samples": int(X.shape[0]),
+                    "epochs": epochs, "mse_log2_ns": loss, "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -208,6 +248,8 @@ def run_gpu(args):
     import graphgen as gg
     import paper_1707_02000_gb300 as pkt
 
+    VARIANTS.update(learned=pkt.VAR_LEARNED, heuristic=pkt.VAR_AUTO, thread=pkt.VAR_THREAD, group=pkt.VAR_GROUP,
+                    warp=pkt.VAR_WARP)
     ws, rank, local = dist_info()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
@@ -230,11 +272,15 @@ def run_gpu(args):
     out = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     loop = {"persistent": pkt.LOOP_PERSISTENT, "plain": pkt.LOOP_PLAIN}[args.loop]
+    variant = VARIANTS[args.variant]
     stream = torch.cuda.current_stream()
+    params, calib = None, None
+    if args.variant == "learned":
+        params, calib = calibrate(pkt, args.workload, CALIB_SEEDS)
 
-    def timed(loop_form, steps, warmup):
+    def timed(loop_form, var, steps, warmup, sched=None):
         for _ in range(warmup):
-            G.decompose(out=out, loop=loop_form, sync=True, stats=True)
+            G.decompose(out=out, loop=loop_form, variant=var, sync=True, stats=True, sched_params=sched)
         barrier()
         per, stats = [], []
         for _ in range(steps):
@@ -242,7 +288,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, st = G.decompose(out=out, loop=loop_form, sync=True, stats=True)
+            _, st = G.decompose(out=out, loop=loop_form, variant=var, sync=True, stats=True, sched_params=sched)
             e1.record(stream)
             e1.synchronize()
             per.append(e0.elapsed_time(e1))
@@ -251,7 +297,7 @@ def run_gpu(args):
         return per, stats
 
     with ClockSampler(local) as clk:
-        per, stats = timed(loop, args.steps, args.warmup)
+        per, stats = timed(loop, variant, args.steps, args.warmup, params)
     total_ms = sum(per)
     if dist is not None:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -263,10 +309,12 @@ def run_gpu(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
     st0 = stats[-1]
     res["config"] = {"workload": f"{args.workload}: {WORKLOAD_DESC}", "m": m, "n": g.n,
-                     "loop": args.loop, "variant": "per-edge heuristic", "vertex_order": "degree",
+                     "loop": args.loop, "variant": VARIANT_DESC[args.variant], "vertex_order": "degree",
                      "l2": "flushed between steps (256 MiB write, untimed)", "replicas": ws,
                      "triangles": st0["triangles"], "t_max": st0["t_max"], "sublevels": st0["sublevels"],
-                     "scans": st0["scans"]}
+                     "scans": st0["scans"], "scanned_entries": st0["scanned"]}
+    if calib is not None:
+        res["config"]["scheduler_calibration"] = calib
     res["gpu_launches"] = int(sum(s["launches"] for s in stats))
     res["clocks"] = clk.summary()
 
@@ -287,12 +335,23 @@ def run_gpu(args):
                        "phases_ms": {"support": ms_sup, "peel": ms_peel},
                        "algorithmic_bytes": {"support": b_sup, "peel": b_peel}}
 
-    if not args.no_plain and args.loop != "plain":
-        pper, pstats = timed(pkt.LOOP_PLAIN, max(1, min(args.steps, 5)), 1)
-        pv = m / (statistics.mean(pper) / 1000.0) * ws
-        res["plain"] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pper),
-                        "speedup_of_reported_form": value / pv,
-                        "launches_per_step": int(statistics.mean(s["launches"] for s in pstats))}
+    if not args.no_plain:
+        # the other forms on the same graph: the host-driven loop with the
+        # fixed heuristic (the baseline form) and, when the reported form is
+        # learned, the persistent loop with the fixed heuristic
+        k = max(3, min(args.steps, 5))
+        others = {}
+        if args.loop != "plain" or args.variant != "heuristic":
+            others["plain"] = (pkt.LOOP_PLAIN, pkt.VAR_AUTO)
+        if args.loop == "persistent" and args.variant != "heuristic":
+            others["persistent_heuristic"] = (pkt.LOOP_PERSISTENT, pkt.VAR_AUTO)
+        for name, (lf, vf) in others.items():
+            pper, pstats = timed(lf, vf, k, 3)
+            pv = m / (statistics.mean(pper) / 1000.0) * ws
+            res[name] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pper), "steps": k,
+                         "speedup_of_reported_form": value / pv,
+                         "ms_peel": statistics.mean(s["ms_peel"] for s in pstats),
+                         "launches_per_step": int(statistics.mean(s["launches"] for s in pstats))}
 
     if not args.no_e2e:
         # the public host-buffer entry point: H2D of the raw edge list from
@@ -301,12 +360,13 @@ def run_gpu(args):
         hd = torch.from_numpy(g.dst).pin_memory()
         ho = torch.empty(g.n_in, dtype=torch.int32).pin_memory()
         hs_np, hd_np, ho_np = hs.numpy(), hd.numpy(), ho.numpy()
-        pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop)
+        pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop, variant=variant, sched_params=params)
         barrier()
         k = max(1, min(args.steps, 5))
         t0 = time.perf_counter()
         for _ in range(k):
-            tau, _ = pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop)
+            tau, _ = pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop, variant=variant,
+                                        sched_params=params)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / k
         res["e2e"] = {"value": m / dt * ws, "unit": UNIT, "h2d_bytes_per_step": int(8 * g.n_in),
@@ -332,6 +392,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--loop", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--variant", default="learned", choices=sorted(VARIANT_DESC))
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -146,19 +146,23 @@ def rand64(seed: int, stream: int, i: int) -> int:
     return int(_load().gg_rand64(seed, stream, i))
 
 
-# The five named workloads (sizes as the paper-class stand-ins use them).
+# The named workloads (sizes as the paper-class stand-ins use them).  Each
+# entry is (generator of a seed, the workload's own seed); another seed gives
+# a graph of the same family and size (calibration inputs).
 WORKLOADS = {
-    "rmat10_ef8": lambda: rmat(10, 8, seed=1),
-    "chunglu_n2^20_d20": lambda: chung_lu(1 << 20, 2.1, 20.0, float(1 << 14), 2),
-    "rgg2d_n2^21_d32": lambda: rgg2d(1 << 21, 32.0, 3),
-    "rmat24_ef16": lambda: rmat(24, 16, seed=4),
+    "rmat10_ef8": (lambda s: rmat(10, 8, seed=s), 1),
+    "chunglu_n2^20_d20": (lambda s: chung_lu(1 << 20, 2.1, 20.0, float(1 << 14), s), 2),
+    "rgg2d_n2^21_d32": (lambda s: rgg2d(1 << 21, 32.0, s), 3),
+    "rmat24_ef16": (lambda s: rmat(24, 16, seed=s), 4),
 }
 BATCH_WORKLOAD = "chunglu_batch4096"
 
 
-def workload(name: str) -> EdgeList:
-    g = WORKLOADS[name]()
-    g.name = name
+def workload(name: str, seed: int | None = None) -> EdgeList:
+    """The named workload; ``seed`` replaces its own seed."""
+    fn, s0 = WORKLOADS[name]
+    g = fn(s0 if seed is None else seed)
+    g.name = name if seed is None or seed == s0 else f"{name}_s{seed}"
     return g
 
 

@@ -126,7 +126,18 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 #define TRUSS_LOOP_PLAIN 0      /* host loop, one launch per phase; the host
                                    reads the frontier size every sub-level */
 #define TRUSS_LOOP_PERSISTENT 1 /* one cooperative kernel, grid barriers with
-                                   a time limit between phases            */
+                                   a time limit between phases; its
+                                   register budget is chosen from the graph:
+                                   the _OCC form when the maximum degree is
+                                   at most 256, else the _LAT form          */
+#define TRUSS_LOOP_PERSISTENT_LAT 2 /* the persistent kernel at 4 blocks of
+                                   256 threads per SM, 64 registers a thread
+                                   (latency-bound peels: many small
+                                   sub-levels of long rows)               */
+#define TRUSS_LOOP_PERSISTENT_OCC 3 /* the persistent kernel at 6 blocks of
+                                   256 threads per SM, 40 registers a thread
+                                   (throughput-bound peels: few large
+                                   sub-levels of short rows)              */
 
 /* ProcessSubLevel work mappings (all exact).  Frontier edges whose shorter
  * adjacency row has more than 32 entries are always cut into fixed-size
@@ -211,7 +222,12 @@ typedef struct truss_stats {
                             support kernel reads (internal vertex order)      */
     int64_t dmin_sum;    /* sum over edges of min(d(u), d(v)): entries of the
                             shorter row that ProcessSubLevel reads            */
-    int64_t reserved[3];
+    int64_t scanned;     /* entries all Scans visited: m for the first Scan,
+                            then the live (unpeeled) edges each later Scan
+                            reads from the compacted list (sync = 1)         */
+    int32_t grid_blocks; /* blocks of the persistent launch (0: plain loop)  */
+    int32_t blocks_per_sm; /* its blocks per SM (4: _LAT form, 6: _OCC)      */
+    int64_t reserved[1];
 } truss_stats;
 
 /* Fill *opts with defaults: persistent loop, heuristic variants, no sync,

@@ -27,7 +27,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP, ETOOBIG
 NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
-LOOP_PLAIN, LOOP_PERSISTENT = 0, 1
+LOOP_PLAIN, LOOP_PERSISTENT, LOOP_PERSISTENT_LAT, LOOP_PERSISTENT_OCC = 0, 1, 2, 3
 VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP, VAR_LEARNED = -1, 0, 1, 2, 3
 SCHED_FEATURES, SCHED_VARIANTS, SCHED_PARAMS, TUNE_CLASSES = 5, 3, 1357, 128
 PROCESSED, IN_CURR = 1, 2
@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("sublevels", ctypes.c_int64), ("scans", ctypes.c_int64),
                 ("triangles", ctypes.c_int64), ("t_max", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("launches", ctypes.c_int64),
-                ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("scanned", ctypes.c_int64),
+                ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -154,6 +155,21 @@ def default_opts(**kw) -> Opts:
     return o
 
 
+def _policy(o: Opts, sched_params, tune_table):
+    """Sets the learned model (device float32[SCHED_PARAMS]) and the tuned
+    table (int8[TUNE_CLASSES]) on ``o``; returns the table array, which the
+    caller keeps alive for the call."""
+    if sched_params is not None:
+        assert sched_params.numel() == SCHED_PARAMS and str(sched_params.dtype) == "torch.float32"
+        assert sched_params.is_cuda and sched_params.is_contiguous()
+        o.sched_params = sched_params.data_ptr()
+    if tune_table is not None:
+        tune_table = np.ascontiguousarray(tune_table, np.int8)
+        assert tune_table.shape == (TUNE_CLASSES,)
+        o.tune_table = tune_table.ctypes.data
+    return tune_table
+
+
 class Graph:
     """A device-resident graph handle (owns its device memory)."""
 
@@ -218,13 +234,7 @@ class Graph:
         out = self._empty(self.m) if out is None else out
         o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record or trace)),
                          level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
-        if sched_params is not None:
-            assert sched_params.numel() == SCHED_PARAMS and str(sched_params.dtype) == "torch.float32"
-            o.sched_params = sched_params.data_ptr()
-        if tune_table is not None:
-            tune_table = np.ascontiguousarray(tune_table, np.int8)
-            assert tune_table.shape == (TUNE_CLASSES,)
-            o.tune_table = tune_table.ctypes.data
+        tune_table = _policy(o, sched_params, tune_table)
         tr = None
         if trace:
             tr = np.zeros(max_sub, TRACE_DTYPE)
@@ -286,7 +296,8 @@ def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = Fal
 
 
 def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool = True, offsets64: bool = False,
-                   out: np.ndarray | None = None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None):
+                   out: np.ndarray | None = None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None,
+                   sched_params=None, tune_table=None):
     """Host arrays in, host trussness out (canonical order): the C ABI's
     truss_decompose_host.  ``src``/``dst`` should be pinned for speed."""
     src = np.ascontiguousarray(src, np.int32)
@@ -296,6 +307,7 @@ def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool 
     flags = (DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
     m = ctypes.c_int64()
     o = default_opts(loop=loop, variant=variant, sync=1)
+    tune_table = _policy(o, sched_params, tune_table)
     st = Stats()
     _check(_lib.truss_decompose_host(src.ctypes.data_as(ctypes.c_void_p), dst.ctypes.data_as(ctypes.c_void_p),
                                      src.shape[0], n, flags, out.ctypes.data_as(ctypes.c_void_p), cap,
@@ -305,7 +317,7 @@ def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool 
 
 
 def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None,
-                    stats: bool = False):
+                    stats: bool = False, sched_params=None, tune_table=None):
     """Decompose many independent graphs (objects with ``n``, ``src``,
     ``dst``; ids local to each graph) in one run on the device.  Returns the
     list of per-graph trussness arrays (CUDA tensors, canonical order of
@@ -322,6 +334,7 @@ def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, var
     out = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
     moff = np.zeros(G + 1, np.int64)
     o = default_opts(loop=loop, variant=variant, sync=1)
+    tune_table = _policy(o, sched_params, tune_table)
     st = Stats()
     _check(_lib.truss_decompose_batch(_dptr(src) if cap else None, _dptr(dst) if cap else None,
                                       eoff.ctypes.data_as(ctypes.c_void_p), nverts.ctypes.data_as(ctypes.c_void_p),

@@ -51,6 +51,7 @@ enum {
     C_NLEVEL = 37,
     C_LAST_L = 38,
     C_TRI = 40,   // [40..41] triangle count (u64), [42] max support
+    C_SCANNED = 44,  // [44..45] entries all Scans visited (i64)
     C_TOTAL = 64
 };
 
@@ -58,7 +59,8 @@ constexpr int PT = 256;      // threads per block in the peel kernels
 constexpr int PW = PT / 32;
 constexpr int LIGHT = 32;    // shorter row <= LIGHT entries: light edge
 constexpr int LCAP = 1024;   // per-block staging of light next-frontier appends
-constexpr int HCAP = PT;     // per-block staging of heavy appends (one per thread at flush)
+constexpr int HPT = 1;       // staged heavy appends per thread at flush
+constexpr int HCAP = PT * HPT;  // per-block staging of heavy appends
 
 // One side of the frontier ping-pong.
 struct Frontier {
@@ -74,9 +76,10 @@ struct PeelSmem {
     int lcnt, hcnt, lbase, hq0;
     uint32_t hb0;
     uint32_t wsum[PT / 32];
+    unsigned long long wtot[PW];  // per-warp packed counts / sums, then offsets
     unsigned long long dsum;  // shorter-row lengths appended by this block
     int dmax;
-    int wcnt[PW];             // block-wide append: per-warp counts, then offsets
+    int wcnt[PW];             // per-warp maxima
     int bbase;
     int bmin[PW];
 };
@@ -139,6 +142,12 @@ __device__ __forceinline__ void write_owner(const Frontier& out, uint32_t ocap, 
         for (uint32_t k = 0; k < n; k++) out.owner[base + k] = (uint32_t)q;
 }
 
+// Next-frontier appends of one block during a sub-level: staged in shared
+// memory and placed by flush() at the end of the phase with one block prefix
+// sum and one atomic per list; entries beyond the stage go to the lists
+// directly.  The shorter-row sum and maximum of the block's appends are kept
+// in shared memory as they arrive, so flush() reads no global memory for
+// light entries.
 struct Appender {
     PeelSmem* sm;
     Frontier out;
@@ -150,69 +159,82 @@ struct Appender {
         const int d = __ldg(dmin + f);
         atomicAdd(&sm->dsum, (unsigned long long)d);
         atomicMax(&sm->dmax, d);
-        int* nl = cnt.nl;
-        unsigned long long* hcp = cnt.hc;
         if (d <= LIGHT) {
             const int p = atomicAdd(&sm->lcnt, 1);
             if (p < LCAP) {
                 sm->lbuf[p] = f;
-            } else {
-                out.light[atomicAdd(nl, 1)] = f;
+                return;
             }
+            out.light[atomicAdd(cnt.nl, 1)] = f;
         } else {
             const int p = atomicAdd(&sm->hcnt, 1);
             if (p < HCAP) {
                 sm->hbuf[p] = f;
-            } else {
-                const uint32_t nch = nchunks_of(d, hc);
-                const unsigned long long old = atomicAdd(hcp, (1ull << 32) | nch);
-                const int q = (int)(old >> 32);
-                out.heavy[q] = f;
-                out.cbase[q] = (uint32_t)old;
-                write_owner(out, ocap, (uint32_t)old, nch, q);
+                return;
             }
+            const uint32_t nch = nchunks_of(d, hc);
+            const unsigned long long old = atomicAdd(cnt.hc, (1ull << 32) | nch);
+            const int q = (int)(old >> 32);
+            out.heavy[q] = f;
+            out.cbase[q] = (uint32_t)old;
+            write_owner(out, ocap, (uint32_t)old, nch, q);
         }
     }
     // whole block; leaves the stage empty
     __device__ void flush() const {
-        int* nl = cnt.nl;
-        unsigned long long* hcp = cnt.hc;
         __syncthreads();
         const int kl = min(sm->lcnt, LCAP), kh = min(sm->hcnt, HCAP);
         const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-        // exclusive scan of the staged heavy edges' chunk counts
-        const uint32_t c = t < kh ? nchunks_of(__ldg(dmin + sm->hbuf[t]), hc) : 0u;
-        uint32_t x = c;
+        // thread t owns staged heavy entries [t * HPT, (t + 1) * HPT)
+        uint32_t c[HPT];
+        uint32_t ct = 0;
+#pragma unroll
+        for (int k = 0; k < HPT; k++) {
+            const int i = t * HPT + k;
+            c[k] = 0;
+            if (i < kh) {
+                c[k] = nchunks_of(__ldg(dmin + sm->hbuf[i]), hc);
+                ct += c[k];
+            }
+        }
+        uint32_t x = ct;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+            const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) sm->wsum[warp] = x;
         __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < PT / 32; w++) {
-            if (w < warp) before += sm->wsum[w];
-            total += sm->wsum[w];
-        }
         if (t == 0) {
+            uint32_t run = 0;
+            for (int w = 0; w < PW; w++) {
+                const uint32_t v = sm->wsum[w];
+                sm->wsum[w] = run;
+                run += v;
+            }
             if (sm->dsum) {
                 atomicAdd(cnt.dsum, sm->dsum);
                 atomicMax(cnt.dmax, sm->dmax);
             }
-            sm->lbase = kl ? atomicAdd(nl, kl) : 0;
+            sm->lbase = kl ? atomicAdd(cnt.nl, kl) : 0;
             if (kh) {
-                const unsigned long long old = atomicAdd(hcp, ((unsigned long long)kh << 32) | total);
+                const unsigned long long old = atomicAdd(cnt.hc, ((unsigned long long)kh << 32) | run);
                 sm->hq0 = (int)(old >> 32);
                 sm->hb0 = (uint32_t)old;
             }
         }
         __syncthreads();
-        for (int i = t; i < kl; i += blockDim.x) out.light[sm->lbase + i] = sm->lbuf[i];
-        if (t < kh) {
-            out.heavy[sm->hq0 + t] = sm->hbuf[t];
-            out.cbase[sm->hq0 + t] = sm->hb0 + before + x - c;
-            write_owner(out, ocap, sm->hb0 + before + x - c, c, sm->hq0 + t);
+        for (int i = t; i < kl; i += PT) out.light[sm->lbase + i] = sm->lbuf[i];
+        uint32_t pc = sm->hb0 + sm->wsum[warp] + x - ct;
+#pragma unroll
+        for (int k = 0; k < HPT; k++) {
+            const int i = t * HPT + k;
+            if (i < kh) {
+                out.heavy[sm->hq0 + i] = sm->hbuf[i];
+                out.cbase[sm->hq0 + i] = pc;
+                write_owner(out, ocap, pc, c[k], sm->hq0 + i);
+                pc += c[k];
+            }
         }
         __syncthreads();
         if (t == 0) {
@@ -235,25 +257,52 @@ __device__ __forceinline__ void smem_init(PeelSmem* sm) {
     __syncthreads();
 }
 
-__device__ __forceinline__ void relax(int2* ss, int32_t f, int32_t l, int32_t g, const Appender& ap) {
-    int a = atomicSub(&ss[f].x, 1);
+// After the decrement of f's support returned a: f enters the next
+// sub-level when it reached l; a value at or below l (pushed there by a racing
+// thread) is restored.
+__device__ __forceinline__ void settle(int2* ss, int32_t f, int a, int32_t l, int32_t g, const Appender& ap) {
     if (a == l + 1) {
         ss[f].y = g + 1;  // f enters the next sub-level
         ap.push(f);
     } else if (a <= l) {
-        atomicAdd(&ss[f].x, 1);  // pushed below l by a racing thread: restore
+        atomicAdd(&ss[f].x, 1);
     }
 }
 
-// Triangle {e1, x, y} seen while processing e1 in sub-level g at level l.
-__device__ __forceinline__ void on_triangle(int2* ss, int32_t e1, int32_t x, int32_t y, int32_t l, int32_t g,
-                                            const Appender& ap) {
-    int2 sx = __ldcg(ss + x);
-    int2 sy = __ldcg(ss + y);
-    if (sx.y < g || sy.y < g) return;  // an edge of it is processed: the triangle is gone
+// Which edges of triangle {e1, x, y} (seen while processing e1 in sub-level g
+// at level l, with x's and y's (S, stamp) pairs sx, sy) lose one support:
+// none when an edge of it is processed; x when S[x] > l and y is not in curr
+// or e1 < y; y likewise.
+__device__ __forceinline__ void decide(int32_t e1, int32_t x, int32_t y, int2 sx, int2 sy, int32_t l, int32_t g,
+                                       bool& dx, bool& dy) {
+    if (sx.y < g || sy.y < g) {
+        dx = dy = false;
+        return;
+    }
     const bool inx = sx.y == g, iny = sy.y == g;
-    if (sx.x > l && (!iny || e1 < y)) relax(ss, x, l, g, ap);
-    if (sy.x > l && (!inx || e1 < x)) relax(ss, y, l, g, ap);
+    dx = sx.x > l && (!iny || e1 < y);
+    dy = sy.x > l && (!inx || e1 < x);
+}
+
+// Two candidate triangles {e1, x1, y1} (ok1) and {e1, x2, y2} (ok2) of one
+// lane; the four edges are distinct, so their loads and decrements are
+// issued together and the round trips overlap.
+__device__ __forceinline__ void on_triangles(int2* ss, int32_t e1, bool ok1, int32_t x1, int32_t y1, bool ok2,
+                                             int32_t x2, int32_t y2, int32_t l, int32_t g, const Appender& ap) {
+    const int2 none = make_int2(0, 0);
+    const int2 sx1 = ok1 ? __ldcg(ss + x1) : none, sy1 = ok1 ? __ldcg(ss + y1) : none;
+    const int2 sx2 = ok2 ? __ldcg(ss + x2) : none, sy2 = ok2 ? __ldcg(ss + y2) : none;
+    bool d1x = false, d1y = false, d2x = false, d2y = false;
+    if (ok1) decide(e1, x1, y1, sx1, sy1, l, g, d1x, d1y);
+    if (ok2) decide(e1, x2, y2, sx2, sy2, l, g, d2x, d2y);
+    const int a1x = d1x ? atomicSub(&ss[x1].x, 1) : 0;
+    const int a1y = d1y ? atomicSub(&ss[y1].x, 1) : 0;
+    const int a2x = d2x ? atomicSub(&ss[x2].x, 1) : 0;
+    const int a2y = d2y ? atomicSub(&ss[y2].x, 1) : 0;
+    if (d1x) settle(ss, x1, a1x, l, g, ap);
+    if (d1y) settle(ss, y1, a1y, l, g, ap);
+    if (d2x) settle(ss, x2, a2x, l, g, ap);
+    if (d2y) settle(ss, y2, a2y, l, g, ap);
 }
 
 template <typename Off>
@@ -270,17 +319,110 @@ __device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
     return Rows<Off>{v0, v1, u0, u1};
 }
 
+// Slots of k1 and k2 in the ascending row a[lo, lo + n) (n >= 1), or -1.
+// Both searches run in lockstep (the step count depends on n only), so each
+// step issues two independent loads.  Each search keeps the last slot whose
+// value is <= its key, with that value, so no load follows the loop.
+template <typename Off>
+__device__ __forceinline__ void find2(const int32_t* __restrict__ a, Off lo, Off n, int32_t k1, int32_t k2, Off& p1,
+                                      Off& p2) {
+    Off b1 = lo, b2 = lo;
+    int32_t v1 = __ldg(a + lo), v2 = v1;
+    while (n > 1) {
+        const Off h = n >> 1;
+        const int32_t t1 = __ldg(a + b1 + h), t2 = __ldg(a + b2 + h);
+        if (t1 <= k1) {
+            b1 += h;
+            v1 = t1;
+        }
+        if (t2 <= k2) {
+            b2 += h;
+            v2 = t2;
+        }
+        n -= h;
+    }
+    p1 = v1 == k1 ? b1 : (Off)-1;
+    p2 = v2 == k2 ? b2 : (Off)-1;
+}
+
 // All triangles through e1 whose apex is one of the slots start, start+step,
-// ... of [a0, a1) (part of the shorter row), each probed in the longer row
-// by binary search.
+// ... of [a0, a1) (part of the shorter row), each probed in the longer row;
+// a lane takes two slots at a time (j and j + step) and searches for both
+// at once.
 template <typename Off>
 __device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a0, Off a1, const Rows<Off>& r,
                                           int start, int step, int32_t l, int32_t g, const Appender& ap) {
-    for (Off j = a0 + start; j < a1; j += step) {
-        int32_t w = __ldg(G.col + j);
-        Off q = find_dev<Off>(G.col, r.b0, r.b1, w);
-        if (q >= 0) on_triangle(G.ss, e1, __ldg(G.eid + j), __ldg(G.eid + q), l, g, ap);
+    for (Off j = a0 + start; j < a1; j += 2 * step) {
+        const Off j2 = j + step;
+        const bool two = j2 < a1;
+        const int32_t w1 = __ldg(G.col + j), x1 = __ldg(G.eid + j);
+        const int32_t w2 = two ? __ldg(G.col + j2) : w1, x2 = two ? __ldg(G.eid + j2) : x1;
+        Off q1, q2;
+        find2<Off>(G.col, r.b0, r.b1 - r.b0, w1, w2, q1, q2);
+        const bool ok1 = q1 >= 0, ok2 = two && q2 >= 0;
+        const int32_t y1 = ok1 ? __ldg(G.eid + q1) : 0, y2 = ok2 ? __ldg(G.eid + q2) : 0;
+        on_triangles(G.ss, e1, ok1, x1, y1, ok2, x2, y2, l, g, ap);
     }
+}
+
+// The same walk for a whole warp on one edge (lanes 0..31 take slots a0 +
+// lane, a0 + lane + 32, ...) when the longer row has at most 32 R entries:
+// the row is loaded once into R registers per lane (coalesced) and each lane
+// binary-searches it through warp shuffles, so a probe costs no memory round
+// trip.  Slot i of the row lives in lane i % 32, register i / 32; slots past
+// the end read as INT_MAX (no vertex id).  Warp-uniform: every lane must call
+// it with the same arguments.
+template <typename Off, int R>
+__device__ __forceinline__ void walk_rows_warp(const Graph<Off>& G, int32_t e1, Off a0, Off a1, const Rows<Off>& r,
+                                               int lane, int32_t l, int32_t g, const Appender& ap) {
+    const int nb = (int)(r.b1 - r.b0);
+    int32_t L[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) L[k] = k * 32 + lane < nb ? __ldg(G.col + r.b0 + k * 32 + lane) : INT_MAX;
+    const int32_t v0 = __shfl_sync(FULL_MASK, L[0], 0);
+    const int rounds = (int)((a1 - a0 + 31) >> 5);
+    for (int t = 0; t < rounds; t++) {
+        const Off j = a0 + (Off)t * 32 + lane;
+        const bool act = j < a1;
+        const int32_t w = act ? __ldg(G.col + j) : INT_MIN;
+        const int32_t x = act ? __ldg(G.eid + j) : 0;
+        // last slot whose value is <= w (slot 0 when none is)
+        int lo = 0;
+        int32_t vlo = v0;
+#pragma unroll
+        for (int h = R * 16; h >= 1; h >>= 1) {
+            const int p = lo + h;
+            int32_t v = __shfl_sync(FULL_MASK, L[0], p & 31);
+#pragma unroll
+            for (int k = 1; k < R; k++) {
+                const int32_t vk = __shfl_sync(FULL_MASK, L[k], p & 31);
+                if ((p >> 5) == k) v = vk;
+            }
+            if (v <= w) {
+                lo = p;
+                vlo = v;
+            }
+        }
+        const bool ok = act && vlo == w;
+        const int32_t y = ok ? __ldg(G.eid + r.b0 + lo) : 0;
+        on_triangles(G.ss, e1, ok, x, y, false, 0, 0, l, g, ap);
+    }
+}
+
+// A warp's walk over [a0, a1) of e1's shorter row: through registers when
+// the longer row is short, else by searches in global memory.  Warp-uniform.
+template <typename Off>
+__device__ __forceinline__ void walk_warp(const Graph<Off>& G, int32_t e1, Off a0, Off a1, const Rows<Off>& r,
+                                          int lane, int32_t l, int32_t g, const Appender& ap) {
+    const Off nb = r.b1 - r.b0;
+    if (nb <= 32)
+        walk_rows_warp<Off, 1>(G, e1, a0, a1, r, lane, l, g, ap);
+    else if (nb <= 64)
+        walk_rows_warp<Off, 2>(G, e1, a0, a1, r, lane, l, g, ap);
+    else if (nb <= 128)
+        walk_rows_warp<Off, 4>(G, e1, a0, a1, r, lane, l, g, ap);
+    else
+        walk_rows<Off>(G, e1, a0, a1, r, lane, 32, l, g, ap);
 }
 
 // Largest q in [0, nh) with cb[q] <= w (cb ascending, cb[0] = 0).
@@ -306,7 +448,10 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
         for (int64_t i = gtid / gsz; i < nl; i += ngrp) {
             const int32_t e1 = __ldcg(cur.light + i);
             const Rows<Off> r = rows_of<Off>(G, e1);
-            walk_rows<Off>(G, e1, r.a0, r.a1, r, sub, gsz, l, g, ap);
+            if (gsz == 32)
+                walk_warp<Off>(G, e1, r.a0, r.a1, r, sub, l, g, ap);
+            else
+                walk_rows<Off>(G, e1, r.a0, r.a1, r, sub, gsz, l, g, ap);
         }
     }
     // heavy chunks: warp w takes the contiguous chunk range [c0, c1), so it
@@ -330,7 +475,7 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
             }
             const int64_t s0 = (int64_t)r.a0 + (int64_t)(c - qb) * G.hc;
             const int64_t s1 = min((int64_t)r.a1, s0 + (int64_t)G.hc);
-            walk_rows<Off>(G, e1, (Off)s0, (Off)s1, r, lane, 32, l, g, ap);
+            walk_warp<Off>(G, e1, (Off)s0, (Off)s1, r, lane, l, g, ap);
         }
     }
 }
@@ -423,15 +568,20 @@ __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const 
 // lists, their stamps <- g; edges with S > l are the live list of the next
 // Scan (`keep`); cnt.minv <- min(cnt.minv, min{S[e] : S[e] > l}).  Edges
 // below l are processed and drop out for good.  Each thread takes SI
-// consecutive list entries per step (16-byte loads where aligned); the
-// survivors of a whole block step are placed with one block prefix sum and
-// one atomic.
+// consecutive list entries per step (16-byte loads where aligned).  A whole
+// block step places its light, heavy and surviving edges with one block
+// prefix sum and at most three atomics (light count; heavy count and chunk
+// total packed in one 64-bit word, which keeps heavy positions and chunk
+// bases in the same order; survivors); the shorter-row sum and maximum are
+// kept per thread and added once per block at the end.
 constexpr int SI = 4;
 
 __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* keep, int32_t l, int32_t g,
                            const Frontier out, const Slot& cnt, const int32_t* dmin, int hc, uint32_t ocap,
                            PeelSmem* sm) {
     int mn = INT_MAX;
+    unsigned long long dsum = 0;
+    int dmax = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * SI;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x * SI; base < nin; base += step) {
@@ -459,49 +609,123 @@ __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* ke
                 sv[k] = ok ? __ldcg(&ss[e[k]].x) : INT_MIN;
             }
         }
-        int nlive = 0;
+        // per thread: light / heavy / survivor counts (SI bits each) and
+        // the heavy edges' chunk total
+        uint32_t c[SI];
+        unsigned nlt = 0, nht = 0, nlv = 0;
+        uint32_t ct = 0;
 #pragma unroll
         for (int k = 0; k < SI; k++) {
-            if (sv[k] == l) ss[e[k]].y = g;
-            if (sv[k] > l) {
+            c[k] = 0;
+            if (sv[k] == l) {
+                ss[e[k]].y = g;
+                const int d = __ldg(dmin + e[k]);
+                dsum += (unsigned)d;
+                dmax = max(dmax, d);
+                if (d <= LIGHT) {
+                    nlt++;
+                } else {
+                    c[k] = nchunks_of(d, hc);
+                    ct += c[k];
+                    nht++;
+                }
+            } else if (sv[k] > l) {
                 mn = min(mn, sv[k]);
-                nlive++;
+                nlv++;
             }
         }
-#pragma unroll
-        for (int k = 0; k < SI; k++) warp_classify_append(sv[k] == l, e[k], dmin, hc, ocap, out, cnt);
-        // survivors: block exclusive scan of per-thread counts, one atomic
-        int x = nlive;
+        // block exclusive prefix of (light, heavy, survivors) packed 16 bits
+        // apiece (a block step holds PT * SI < 2^16 entries) and of chunks
+        unsigned long long x = (unsigned long long)nlt | ((unsigned long long)nht << 16) |
+                               ((unsigned long long)nlv << 32);
+        uint32_t xc = ct;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL_MASK, x, o);
-            if (lane >= o) x += y;
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, x, o);
+            const uint32_t yc = __shfl_up_sync(FULL_MASK, xc, o);
+            if (lane >= o) {
+                x += y;
+                xc += yc;
+            }
         }
-        if (lane == 31) sm->wcnt[warp] = x;
+        if (lane == 31) {
+            sm->wtot[warp] = x;
+            sm->wsum[warp] = xc;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int run = 0;
+            unsigned long long run = 0;
+            uint32_t runc = 0;
             for (int w = 0; w < PW; w++) {
-                const int c = sm->wcnt[w];
-                sm->wcnt[w] = run;
-                run += c;
+                const unsigned long long t = sm->wtot[w];
+                const uint32_t tc = sm->wsum[w];
+                sm->wtot[w] = run;
+                sm->wsum[w] = runc;
+                run += t;
+                runc += tc;
             }
-            sm->bbase = run ? atomicAdd(cnt.nlive, run) : 0;
+            const int tl = (int)(run & 0xffff), th = (int)((run >> 16) & 0xffff), tv = (int)(run >> 32);
+            sm->lbase = tl ? atomicAdd(cnt.nl, tl) : 0;
+            if (th) {
+                const unsigned long long old = atomicAdd(cnt.hc, ((unsigned long long)th << 32) | runc);
+                sm->hq0 = (int)(old >> 32);
+                sm->hb0 = (uint32_t)old;
+            }
+            sm->bbase = tv ? atomicAdd(cnt.nlive, tv) : 0;
         }
         __syncthreads();
-        int pos = sm->bbase + sm->wcnt[warp] + x - nlive;
+        const unsigned long long ex = sm->wtot[warp] + x -
+                                      ((unsigned long long)nlt | ((unsigned long long)nht << 16) |
+                                       ((unsigned long long)nlv << 32));
+        int pl = sm->lbase + (int)(ex & 0xffff);
+        int ph = sm->hq0 + (int)((ex >> 16) & 0xffff);
+        int pv = sm->bbase + (int)(ex >> 32);
+        uint32_t pc = sm->hb0 + sm->wsum[warp] + xc - ct;
 #pragma unroll
-        for (int k = 0; k < SI; k++)
-            if (sv[k] > l) keep[pos++] = e[k];
+        for (int k = 0; k < SI; k++) {
+            if (sv[k] == l) {
+                if (c[k] == 0) {
+                    out.light[pl++] = e[k];
+                } else {
+                    out.heavy[ph] = e[k];
+                    out.cbase[ph] = pc;
+                    write_owner(out, ocap, pc, c[k], ph);
+                    ph++;
+                    pc += c[k];
+                }
+            } else if (sv[k] > l) {
+                keep[pv++] = e[k];
+            }
+        }
+        // no barrier needed here: a warp's shuffles in the next step (or
+        // below) come after all its lanes read their offsets, and thread 0
+        // rewrites the shared offsets only after the next step's barrier
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
-    if (lane == 0) sm->bmin[warp] = mn;
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
+        dmax = max(dmax, __shfl_xor_sync(FULL_MASK, dmax, o));
+    }
+    dsum = warp_sum(dsum);
+    if (lane == 0) {
+        sm->bmin[warp] = mn;
+        sm->wtot[warp] = dsum;
+        sm->wcnt[warp] = dmax;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int b = INT_MAX;
-        for (int w = 0; w < PW; w++) b = min(b, sm->bmin[w]);
+        int b = INT_MAX, bm = 0;
+        unsigned long long bs = 0;
+        for (int w = 0; w < PW; w++) {
+            b = min(b, sm->bmin[w]);
+            bm = max(bm, sm->wcnt[w]);
+            bs += sm->wtot[w];
+        }
         if (b != INT_MAX) atomicMin(cnt.minv, b);
+        if (bs) {
+            atomicAdd(cnt.dsum, bs);
+            atomicMax(cnt.dmax, bm);
+        }
     }
     __syncthreads();
 }
@@ -561,19 +785,23 @@ __device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns, un
         v += 1;
         int ok = 1;
         if ((int)(v - target) < 0) {
+            // tight poll; the error word and the clock are read at polls
+            // 1, 2, 4, ..., 256 and then every 256 (each read is another L2
+            // round trip; the early reads let short limits take effect)
             const uint64_t t0 = global_ns();
-            for (;;) {
-                __nanosleep(16);
+            for (unsigned spin = 1;; spin++) {
                 v = ld_acquire_gpu_u32(count);
                 if ((int)(v - target) >= 0) break;
-                if (ld_acquire_gpu(ctr + C_ERR) != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicCAS(ctr + C_ERR, 0, TRUSS_ETIMEOUT);
-                    ok = 0;
-                    break;
+                if ((spin & (spin - 1)) == 0 || (spin & 255u) == 0) {
+                    if (ld_acquire_gpu(ctr + C_ERR) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > timeout_ns) {
+                        atomicCAS(ctr + C_ERR, 0, TRUSS_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
         }
@@ -601,11 +829,12 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // writes its counters to slot p & 3; slot (p+2) & 3 is cleared during phase
 // p: its last readers read it right after the barrier that ended phase p-2,
 // and the barrier ending phase p-1 lies in between.
-// Six blocks per SM (at most 40 registers): measured against 4-8 blocks on
-// the power-law and geometric workloads, it balances occupancy for big
-// throughput-bound frontiers against spills on the latency-bound path.
-template <typename Off>
-__global__ void __launch_bounds__(PT, 6)
+// MINB blocks per SM: 6 (at most 40 registers a thread) gives the warps that
+// large frontiers of short rows need; 4 (64 registers, no spills) runs the
+// dependent-load chains of many small sub-levels of long rows fastest.
+// Measured on the power-law and geometric workloads against 5 and 7.
+template <typename Off, int MINB>
+__global__ void __launch_bounds__(PT, MINB)
     k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
                  int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace,
                  const float* sched, TuneTable tt) {
@@ -620,6 +849,7 @@ __global__ void __launch_bounds__(PT, 6)
     int32_t l = 0, g = 0;
     int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0, p = 0;
     int64_t nlive = G.m;  // edges the next Scan visits
+    int64_t scanned = 0;
     uint64_t scan_ns = 0;
     while (processed < G.m) {
         uint64_t ts = 0;
@@ -631,6 +861,7 @@ __global__ void __launch_bounds__(PT, 6)
         int s = (int)(p & 3);
         const int32_t* lin = sc == 0 ? nullptr : ((sc & 1) ? live0 : live1);
         int32_t* lout = (sc & 1) ? live1 : live0;
+        scanned += nlive;
         scan_level(G.ss, lin, nlive, lout, l, g, cur, slot_of(ctr, s), G.dmin, G.hc, G.ocap, &sm);
         if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, s, &sv)) return;
         if (leader) scan_ns += global_ns() - ts;
@@ -700,6 +931,7 @@ __global__ void __launch_bounds__(PT, 6)
         ctr[C_NSCAN] = (int)sc;
         ctr[C_NLEVEL] = (int)nlevel;
         ctr[C_LAST_L] = l;
+        *reinterpret_cast<long long*>(ctr + C_SCANNED) = scanned;
     }
 }
 
@@ -816,7 +1048,7 @@ Frontier side(truss_graph* g, int k) {
 }
 
 struct RunOut {
-    int64_t nsub = 0, nscan = 0, nlevel = 0;
+    int64_t nsub = 0, nscan = 0, nlevel = 0, scanned = 0;
     int32_t last_l = 0;
 };
 
@@ -855,6 +1087,7 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
         k_init_counters<<<1, 64, 0, s>>>(ctr);
         if (trace) CU(cudaEventRecord(e0, s));
         k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc, g->ocap);
+        out->scanned += nlive;
         if (trace) CU(cudaEventRecord(e1, s));
         CU(cudaGetLastError());
         truss_note_launch(2);
@@ -912,14 +1145,23 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
     return rc;
 }
 
-template <typename Off>
-int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
-                   int64_t max_trace) {
+// Blocks per SM of the persistent form for options o on graph g.
+inline int persistent_minb(const truss_graph* g, const truss_opts& o) {
+    if (o.loop == TRUSS_LOOP_PERSISTENT_LAT) return 4;
+    if (o.loop == TRUSS_LOOP_PERSISTENT_OCC) return 6;
+    return g->max_deg <= 256 ? 6 : 4;
+}
+
+template <typename Off, int MINB>
+int launch_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
+                      int64_t max_trace) {
     Graph<Off> G = graph_view<Off>(g);
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<Off>, PT, 0));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<Off, MINB>, PT, 0));
     if (per_sm < 1) return TRUSS_ENOTSUP;
     int blocks = per_sm * g->sms;
+    g->last_grid = blocks;
+    g->last_per_sm = per_sm;
     k_init_counters<<<1, 64, 0, s>>>(g->ctr);
     CU(cudaGetLastError());
     int variant = o.variant;
@@ -932,13 +1174,20 @@ int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_su
     const float* sched = o.sched_params;
     TuneTable tt = tune_table_of(o);
     void* args[] = {&G, &f0, &f1, &live0, &live1, &ctr, &variant, &jump, &tmo, &d_trace, &max_trace, &sched, &tt};
-    CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off>, dim3(blocks), dim3(PT), args, 0, s));
+    CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off, MINB>, dim3(blocks), dim3(PT), args, 0, s));
     truss_note_launch(2);
     return TRUSS_OK;
 }
 
+template <typename Off>
+int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
+                   int64_t max_trace) {
+    if (persistent_minb(g, o) == 4) return launch_persistent<Off, 4>(g, o, s, d_trace, max_trace);
+    return launch_persistent<Off, 6>(g, o, s, d_trace, max_trace);
+}
+
 int check_opts(const truss_opts& o) {
-    if (o.loop != TRUSS_LOOP_PLAIN && o.loop != TRUSS_LOOP_PERSISTENT) return TRUSS_EINVAL;
+    if (o.loop < TRUSS_LOOP_PLAIN || o.loop > TRUSS_LOOP_PERSISTENT_OCC) return TRUSS_EINVAL;
     if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_LEARNED) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size)) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_trace) && (o.max_sub < 0 || !o.sync)) return TRUSS_EINVAL;
@@ -975,13 +1224,17 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         if (rec) CU(cudaMallocAsync((void**)&d_tr, sizeof(truss_sublevel_trace) * (size_t)o.max_sub, s));
         rc = run_persistent<Off>(g, o, s, d_tr, rec ? o.max_sub : 0);
         if (rc == TRUSS_OK && o.sync) {
+            // the triangle words (C_TRI on) keep the support phase's count on
+            // the host side; the peel cleared them on the device
             CU(cudaMemcpyAsync(g->h_ctr, g->ctr, sizeof(int) * C_TRI, cudaMemcpyDeviceToHost, s));
+            CU(cudaMemcpyAsync(g->h_ctr + C_SCANNED, g->ctr + C_SCANNED, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             if (g->h_ctr[C_ERR]) rc = g->h_ctr[C_ERR];
             ro.nsub = g->h_ctr[C_NSUB];
             ro.nscan = g->h_ctr[C_NSCAN];
             ro.nlevel = g->h_ctr[C_NLEVEL];
             ro.last_l = g->h_ctr[C_LAST_L];
+            memcpy(&ro.scanned, g->h_ctr + C_SCANNED, sizeof(ro.scanned));
             if (rec && rc == TRUSS_OK) {
                 const int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
                 CU(cudaMemcpyAsync(htr.data(), d_tr, sizeof(truss_sublevel_trace) * (size_t)k, cudaMemcpyDeviceToHost, s));
@@ -1026,6 +1279,9 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         st->launches = truss_launch_count() - launches0;
         st->wedges_up = g->wedges_up;
         st->dmin_sum = g->dmin_sum;
+        st->scanned = ro.scanned;
+        st->grid_blocks = o.loop == TRUSS_LOOP_PLAIN ? 0 : g->last_grid;
+        st->blocks_per_sm = o.loop == TRUSS_LOOP_PLAIN ? 0 : g->last_per_sm;
         if (o.sync) {
             unsigned long long tri = 0;
             memcpy(&tri, g->h_ctr + C_TRI, sizeof(tri));
@@ -1097,9 +1353,9 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 int truss_ensure_workspace(truss_graph* g) {
     if (g->ctr) return TRUSS_OK;
     const size_t m = (size_t)(g->m > 0 ? g->m : 1);
-    // heavy chunk length: 32 entries, longer when the graph is so large that
-    // a sub-level's chunk total could leave 32 bits
-    int64_t hc = 32;
+    // heavy chunk length: 64 entries (two per lane), longer when the graph is
+    // so large that a sub-level's chunk total could leave 32 bits
+    int64_t hc = 64;
     while ((int64_t)g->m + g->dmin_sum / hc >= ((int64_t)1 << 32) - 1) hc *= 2;
     g->hc = (int)hc;
     CU(cudaMalloc((void**)&g->ss, sizeof(int2) * (m + 1)));

@@ -100,12 +100,15 @@ def test_edge_list_and_support(pkt, name, g, relabel, off64):
 
 # ------------------------------------------------------------ decomposition
 
-LOOPS = ["plain", "persistent"]
+# the persistent kernel in both register budgets (the automatic choice picks
+# one of them per graph)
+LOOPS = ["plain", "persistent_lat", "persistent_occ"]
 VARIANTS = ["auto", "thread", "group", "warp"]
 
 
 def _loop(pkt, name):
-    return {"plain": pkt.LOOP_PLAIN, "persistent": pkt.LOOP_PERSISTENT}[name]
+    return {"plain": pkt.LOOP_PLAIN, "persistent": pkt.LOOP_PERSISTENT, "persistent_lat": pkt.LOOP_PERSISTENT_LAT,
+            "persistent_occ": pkt.LOOP_PERSISTENT_OCC}[name]
 
 
 def _var(pkt, name):
@@ -316,6 +319,62 @@ def test_stats(pkt):
     assert st["m"] == eu.size
     _, lv, sz = oracle.pkt_serial(g.n, eu, ev)
     assert st["sublevels"] == sz.size and st["levels"] == np.unique(lv).size
+
+
+def _scan_sequence(m, tau, step):
+    """Levels of the Scans of Algorithm 4 with level jumps (an empty Scan
+    jumps to the smallest live support), and the entries each visits: all m
+    for the first, then the survivors of the one before -- edges of a higher
+    level, plus edges of its own level that entered a later sub-level than
+    the Scan's frontier."""
+    L = tau.astype(np.int64) - 2
+    levels = np.unique(L)
+    first = {int(l): int(step[L == l].min()) for l in levels}
+    seq, l, done = [], 0, 0
+    while done < m:
+        seq.append(l)
+        if l in first:
+            done += int((L == l).sum())
+            l += 1
+        else:
+            l = int(levels[levels > l].min())
+    surv = lambda l: int((L > l).sum()) + (int(((L == l) & (step != first[l])).sum()) if l in first else 0)
+    visited = [m] + [surv(x) for x in seq[:-1]]
+    return seq, visited
+
+
+def test_persistent_form_choice(pkt):
+    """The automatic persistent form takes 6 blocks per SM for graphs whose
+    rows are all short and 4 otherwise; forced forms are honoured; every
+    form gives the oracle's trussness."""
+    import torch
+
+    for g, want_bps in ((gg.rgg2d(30000, 20.0, seed=5), 6), (gg.chung_lu(30000, 2.1, 12.0, 3000.0, seed=6), 4)):
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+        want = oracle.truss_of_edges(g.n, g.src, g.dst)[2]
+        for loop, bps in ((pkt.LOOP_PERSISTENT, want_bps), (pkt.LOOP_PERSISTENT_LAT, 4),
+                          (pkt.LOOP_PERSISTENT_OCC, 6)):
+            tau, st = G.decompose(loop=loop, stats=True)
+            assert np.array_equal(host(tau), want)
+            assert st["blocks_per_sm"] == bps
+            assert st["grid_blocks"] == bps * torch.cuda.get_device_properties(0).multi_processor_count
+        _, st = G.decompose(loop=pkt.LOOP_PLAIN, stats=True)
+        assert st["grid_blocks"] == 0 and st["blocks_per_sm"] == 0
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_scan_counts_match_the_live_list(pkt, loop):
+    """Scans and scanned entries reported by the library equal the counts
+    the serial run implies: each Scan after the first visits exactly the
+    edges the previous one kept."""
+    for g in (gg.workload("rmat10_ef8"), gg.chung_lu(3000, 2.1, 14.0, 300.0, seed=8)):
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+        _, st = G.decompose(loop=_loop(pkt, loop), stats=True)
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        want, _, _, ostep = oracle.pkt_serial(g.n, eu, ev, return_steps=True)
+        seq, visited = _scan_sequence(eu.size, want, ostep)
+        assert st["scans"] == len(seq)
+        assert st["scanned"] == sum(visited), (st["scanned"], sum(visited))
 
 
 @pytest.mark.parametrize("loop", LOOPS)
