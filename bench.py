@@ -271,7 +271,7 @@ def run_gpu(args):
     m = G.m
     out = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    loop = {"persistent": pkt.LOOP_PERSISTENT, "plain": pkt.LOOP_PLAIN}[args.loop]
+    loop = {"persistent": pkt.LOOP_PERSISTENT, "plain": pkt.LOOP_PLAIN, "graph": pkt.LOOP_GRAPH}[args.loop]
     variant = VARIANTS[args.variant]
     stream = torch.cuda.current_stream()
     params, calib = None, None
@@ -324,7 +324,8 @@ def run_gpu(args):
     b_sup, b_peel = algorithmic_bytes(st0, g.n)
     peak, peak_kind = peaks()
     if ms_peel >= ms_sup:
-        kname, b, ms = ("k_persistent" if args.loop == "persistent" else "k_process"), b_peel, ms_peel
+        kname = {"persistent": "k_persistent", "plain": "k_process", "graph": "k_gprocess"}[args.loop]
+        b, ms = b_peel, ms_peel
     else:
         kname, b, ms = "k_support_warp", b_sup, ms_sup
     ach = b / (ms / 1000.0) / 1e9
@@ -337,14 +338,17 @@ def run_gpu(args):
 
     if not args.no_plain:
         # the other forms on the same graph: the host-driven loop with the
-        # fixed heuristic (the baseline form) and, when the reported form is
-        # learned, the persistent loop with the fixed heuristic
+        # fixed heuristic (the baseline form), the graph-driven loop and,
+        # when the reported form is learned, the persistent loop with the
+        # fixed heuristic
         k = max(3, min(args.steps, 5))
         others = {}
         if args.loop != "plain" or args.variant != "heuristic":
             others["plain"] = (pkt.LOOP_PLAIN, pkt.VAR_AUTO)
         if args.loop == "persistent" and args.variant != "heuristic":
             others["persistent_heuristic"] = (pkt.LOOP_PERSISTENT, pkt.VAR_AUTO)
+        if args.loop != "graph":
+            others["graph"] = (pkt.LOOP_GRAPH, pkt.VAR_AUTO)
         for name, (lf, vf) in others.items():
             pper, pstats = timed(lf, vf, k, 3)
             pv = m / (statistics.mean(pper) / 1000.0) * ws
@@ -391,7 +395,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--loop", default="persistent", choices=["persistent", "plain"])
+    ap.add_argument("--loop", default="persistent", choices=["persistent", "plain", "graph"])
     ap.add_argument("--variant", default="learned", choices=sorted(VARIANT_DESC))
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

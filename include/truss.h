@@ -128,8 +128,13 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 #define TRUSS_LOOP_PERSISTENT 1 /* one cooperative kernel, grid barriers with
                                    a time limit between phases; its
                                    register budget is chosen from the graph:
-                                   the _OCC form when the maximum degree is
-                                   at most 256, else the _LAT form          */
+                                   the _OCC form when the shorter-row entries
+                                   the peel walks, W = sum_e min(d(u), d(v)),
+                                   reach 2^24 per support level (W over the
+                                   largest support + 1) or 2^34 in all, else
+                                   the _LAT form.  The call waits for the
+                                   support phase to read the largest support
+                                   (the forced forms below do not wait)    */
 #define TRUSS_LOOP_PERSISTENT_LAT 2 /* the persistent kernel at 4 blocks of
                                    256 threads per SM, 64 registers a thread
                                    (latency-bound peels: many small
@@ -138,6 +143,14 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
                                    256 threads per SM, 40 registers a thread
                                    (throughput-bound peels: few large
                                    sub-levels of short rows)              */
+#define TRUSS_LOOP_GRAPH 4      /* one CUDA graph: a conditional while node
+                                   whose body runs a one-block control
+                                   kernel that picks the next phase on the
+                                   device, then a switch node with the Scan
+                                   or the ProcessSubLevel kernel; no host
+                                   round trip between phases.  The limit
+                                   (timeout_ns) applies to each phase, and
+                                   the phases are bounded by 2m + dmax + 64 */
 
 /* ProcessSubLevel work mappings (all exact).  Frontier edges whose shorter
  * adjacency row has more than 32 entries are always cut into fixed-size
@@ -227,7 +240,9 @@ typedef struct truss_stats {
                             reads from the compacted list (sync = 1)         */
     int32_t grid_blocks; /* blocks of the persistent launch (0: plain loop)  */
     int32_t blocks_per_sm; /* its blocks per SM (4: _LAT form, 6: _OCC)      */
-    int64_t reserved[1];
+    int32_t max_support; /* largest support before peeling (set when stats
+                            are requested or the form is chosen)           */
+    int32_t reserved;
 } truss_stats;
 
 /* Fill *opts with defaults: persistent loop, heuristic variants, no sync,

@@ -27,7 +27,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP, ETOOBIG
 NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
-LOOP_PLAIN, LOOP_PERSISTENT, LOOP_PERSISTENT_LAT, LOOP_PERSISTENT_OCC = 0, 1, 2, 3
+LOOP_PLAIN, LOOP_PERSISTENT, LOOP_PERSISTENT_LAT, LOOP_PERSISTENT_OCC, LOOP_GRAPH = 0, 1, 2, 3, 4
 VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP, VAR_LEARNED = -1, 0, 1, 2, 3
 SCHED_FEATURES, SCHED_VARIANTS, SCHED_PARAMS, TUNE_CLASSES = 5, 3, 1357, 128
 PROCESSED, IN_CURR = 1, 2
@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("triangles", ctypes.c_int64), ("t_max", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("launches", ctypes.c_int64),
                 ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("scanned", ctypes.c_int64),
-                ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int64)]
+                ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("max_support", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

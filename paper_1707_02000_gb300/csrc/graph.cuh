@@ -58,6 +58,7 @@ struct truss_graph {
     int32_t n_sup_huge = 0;
     int64_t max_deg = 0;
     int last_grid = 0, last_per_sm = 0;  // blocks of the last persistent launch
+    void* gctl = nullptr;   // state of the graph-driven level loop
     int64_t max_updeg = 0;
     int64_t wedges_up = 0;  // sum_v d-(v) d+(v)
     int64_t dmin_sum = 0;   // sum_e min(d(u), d(v))

@@ -1145,11 +1145,282 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
     return rc;
 }
 
-// Blocks per SM of the persistent form for options o on graph g.
-inline int persistent_minb(const truss_graph* g, const truss_opts& o) {
+// ------------------------------------------------- graph-driven level loop
+
+// Algorithm 4's loop as one CUDA graph: a while node whose body runs a
+// one-block control kernel and then a switch node holding the Scan kernel
+// (case 0) and the ProcessSubLevel kernel (case 1).  The control kernel
+// reads the counters of the phase that just ran, decides the next phase
+// exactly as the host loop and the persistent kernel do, and sets both
+// conditions; no host round trip and no grid barrier between phases.  Every
+// phase is a separate kernel, so the state lives in device memory (GCtl).
+enum { PH_SCAN = 0, PH_SUB = 1, PH_DONE = 2, PH_FIRST = -1 };
+
+struct GCtl {
+    int32_t type;      // phase the body runs now (PH_*)
+    int32_t l, g;      // level, sub-level number (the stamp of curr)
+    int32_t nl, nh;    // frontier of the sub-level
+    int32_t gsz;       // lanes per light edge
+    int32_t slot;      // counter slot the phase writes (0 or 1)
+    int32_t err;
+    int32_t dmax;
+    uint32_t nchunk;
+    int64_t dsum;
+    int64_t processed, nsub, nscan, nlevel;
+    int64_t nlive;     // entries the next Scan visits
+    int64_t scanned;
+    int64_t phases, cap;  // phases run, and the bound on them
+    uint64_t t_phase;  // start of the phase that is running
+    uint64_t scan_ns;  // Scan time since the last sub-level
+    uint64_t timeout;  // limit on one phase
+};
+
+__global__ void k_ginit(GCtl* c, int* ctr, int64_t m, int64_t cap, uint64_t timeout) {
+    for (int i = threadIdx.x; i < C_TOTAL; i += blockDim.x) ctr[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < 4) clear_slot_vals(slots(ctr) + threadIdx.x);
+    if (threadIdx.x == 0) {
+        GCtl s;
+        memset(&s, 0, sizeof(s));
+        s.type = PH_FIRST;
+        s.slot = 1;
+        s.nlive = m;
+        s.cap = cap;
+        s.timeout = timeout;
+        *c = s;
+    }
+}
+
+// One warp.  Thread 0 runs the state machine; the whole warp evaluates the
+// learned model when it is consulted.
+__global__ void __launch_bounds__(32) k_gctl(GCtl* c, int* ctr, int64_t m, int variant, int level_jump,
+                                             truss_sublevel_trace* trace, int64_t max_trace, const float* sched,
+                                             TuneTable tt, cudaGraphConditionalHandle wh,
+                                             cudaGraphConditionalHandle sh) {
+    __shared__ GCtl s;
+    if (threadIdx.x == 0) {
+        const uint64_t now = global_ns();
+        s = *c;
+        if (s.type == PH_FIRST) {
+            s.type = m > 0 ? PH_SCAN : PH_DONE;
+        } else {
+            SlotVals v;
+            memcpy(&v, slots(ctr) + s.slot, sizeof(v));
+            const int vnh = (int)(v.hc >> 32);
+            if (now - s.t_phase > s.timeout) s.err = TRUSS_ETIMEOUT;
+            if (s.type == PH_SCAN) {
+                s.nscan++;
+                s.scanned += s.nlive;
+                s.nlive = v.nlive;
+                s.scan_ns += now - s.t_phase;
+                if (v.nl + vnh == 0) {
+                    if (v.minv == INT_MAX) {
+                        s.type = PH_DONE;
+                    } else {
+                        s.l = level_jump ? v.minv : s.l + 1;
+                    }
+                } else {
+                    s.nlevel++;
+                    s.type = PH_SUB;
+                }
+            } else {  // a sub-level just ran
+                if (trace && s.nsub - 1 < max_trace) trace[s.nsub - 1].t_ns = (int64_t)(now - s.t_phase);
+                s.g++;
+                if (v.nl + vnh == 0) {
+                    s.l++;
+                    s.type = s.processed < m ? PH_SCAN : PH_DONE;
+                }
+            }
+            if (s.type == PH_SUB) {
+                s.nl = v.nl;
+                s.nh = vnh;
+                s.nchunk = (uint32_t)v.hc;
+                s.dsum = (int64_t)v.dsum;
+                s.dmax = v.dmax;
+            }
+        }
+        s.phases++;
+        if (s.type != PH_DONE && s.phases > s.cap) s.err = TRUSS_ETIMEOUT;
+        if (s.err) s.type = PH_DONE;
+        s.gsz = s.type == PH_SUB ? pick_group(variant, s.nl, s.dsum, (int64_t)s.nl + s.nh, tt) : 0;
+    }
+    __syncwarp();
+    if (s.type == PH_SUB && variant == TRUSS_VAR_LEARNED && sched && s.nl >= LEARN_MIN_LIGHT) {
+        float x[SF];
+        sched_features((int64_t)s.nl + s.nh, s.dsum, s.dmax, s.l, m - s.processed, x);
+        const int ch = sched_pick(sched, x);
+        if (threadIdx.x == 0 && ch >= 0) s.gsz = group_of(ch);
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (s.type == PH_SUB) {
+            if (trace && s.nsub < max_trace) {
+                truss_sublevel_trace& r = trace[s.nsub];
+                r.level = s.l;
+                r.group = s.gsz;
+                r.n_light = s.nl;
+                r.n_heavy = s.nh;
+                r.n_chunks = s.nchunk;
+                r.dmax = s.dmax;
+                r.dsum = s.dsum;
+                r.todo = m - s.processed;
+                r.t_ns = 0;
+                r.scan_ns = (int64_t)s.scan_ns;
+            }
+            s.scan_ns = 0;
+            s.processed += (int64_t)s.nl + s.nh;
+            s.nsub++;
+        }
+        s.slot ^= 1;
+        clear_slot_vals(slots(ctr) + s.slot);
+        if (s.type == PH_DONE) {
+            ctr[C_NSUB] = (int)s.nsub;
+            ctr[C_NSCAN] = (int)s.nscan;
+            ctr[C_NLEVEL] = (int)s.nlevel;
+            ctr[C_LAST_L] = s.l;
+            *reinterpret_cast<long long*>(ctr + C_SCANNED) = s.scanned;
+            if (s.err) ctr[C_ERR] = s.err;
+        }
+        s.t_phase = global_ns();
+        *c = s;
+        cudaGraphSetConditional(sh, (unsigned)s.type);  // PH_DONE (2) runs no case
+        cudaGraphSetConditional(wh, s.type != PH_DONE ? 1u : 0u);
+    }
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(PT) k_gscan(Graph<Off> G, const GCtl* c, Frontier f0, Frontier f1,
+                                              int32_t* live0, int32_t* live1, int* ctr) {
+    __shared__ PeelSmem sm;
+    smem_init(&sm);
+    const int64_t sc = c->nscan, nin = c->nlive;
+    const int32_t l = c->l, g = c->g;
+    const int slot = c->slot;
+    const int32_t* lin = sc == 0 ? nullptr : ((sc & 1) ? live0 : live1);
+    int32_t* lout = (sc & 1) ? live1 : live0;
+    scan_level(G.ss, lin, nin, lout, l, g, (g & 1) ? f1 : f0, slot_of(ctr, slot), G.dmin, G.hc, G.ocap, &sm);
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(PT) k_gprocess(Graph<Off> G, const GCtl* c, Frontier f0, Frontier f1, int* ctr) {
+    __shared__ PeelSmem sm;
+    smem_init(&sm);
+    const int nl = c->nl, nh = c->nh, gsz = c->gsz, slot = c->slot;
+    const uint32_t nchunk = c->nchunk;
+    const int32_t l = c->l, g = c->g;
+    const Frontier cu = (g & 1) ? f1 : f0, nx = (g & 1) ? f0 : f1;
+    const Appender ap{&sm, nx, slot_of(ctr, slot), G.dmin, G.hc, G.ocap};
+    process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
+    ap.flush();
+}
+
+// Builds, launches and releases the graph of one decomposition's peel (the
+// executable graph is freed by the runtime once it has run).
+template <typename Off>
+int run_graph(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
+              int64_t max_trace) {
+    Graph<Off> G = graph_view<Off>(g);
+    GCtl* c = reinterpret_cast<GCtl*>(g->gctl);
+    int* ctr = g->ctr;
+    int64_t m = g->m;
+    const int sblocks = grid_for((g->m + 1) / 2, PT, (int64_t)g->sms * 8);
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gprocess<Off>, PT, 0));
+    const int pblocks = std::max(1, per_sm) * g->sms;
+    g->last_grid = pblocks;
+    g->last_per_sm = std::max(1, per_sm);
+    // a bound on the phases: at most m sub-levels, m non-empty Scans and one
+    // empty Scan per support level
+    const int64_t cap = 2 * g->m + g->max_deg + 64;
+    const uint64_t tmo = o.timeout_ns > 0 ? (uint64_t)o.timeout_ns : 10000000000ull;
+    k_ginit<<<1, 64, 0, s>>>(c, ctr, m, cap, tmo);
+    CU(cudaGetLastError());
+    truss_note_launch();
+
+    int variant = o.variant;
+    int jump = o.level_jump;
+    const float* sched = o.sched_params;
+    TuneTable tt = tune_table_of(o);
+    Frontier f0 = side(g, 0), f1 = side(g, 1);
+    int32_t* live0 = g->live[0];
+    int32_t* live1 = g->live[1];
+    cudaGraph_t top = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = TRUSS_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == TRUSS_OK) {
+            truss_note_cuda_error(e);
+            rc = e == cudaErrorMemoryAllocation ? TRUSS_ENOMEM : TRUSS_ECUDA;
+        }
+        return rc == TRUSS_OK;
+    };
+    do {
+        if (!ok(cudaGraphCreate(&top, 0))) break;
+        cudaGraphConditionalHandle wh, sh;
+        if (!ok(cudaGraphConditionalHandleCreate(&wh, top, 1, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = wh;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wn;
+        if (!ok(cudaGraphAddNode(&wn, top, nullptr, nullptr, 0, &wp))) break;
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if (!ok(cudaGraphConditionalHandleCreate(&sh, body, PH_DONE, cudaGraphCondAssignDefault))) break;
+        void* cargs[] = {&c, &ctr, &m, &variant, &jump, &d_trace, &max_trace, &sched, &tt, &wh, &sh};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)k_gctl;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = cargs;
+        cudaGraphNode_t cn;
+        if (!ok(cudaGraphAddKernelNode(&cn, body, nullptr, 0, &kp))) break;
+        cudaGraphNodeParams sp = {};
+        sp.type = cudaGraphNodeTypeConditional;
+        sp.conditional.handle = sh;
+        sp.conditional.type = cudaGraphCondTypeSwitch;
+        sp.conditional.size = 2;
+        cudaGraphNode_t sn;
+        if (!ok(cudaGraphAddNode(&sn, body, &cn, nullptr, 1, &sp))) break;
+        const GCtl* cc = c;
+        void* sargs[] = {&G, &cc, &f0, &f1, &live0, &live1, &ctr};
+        cudaKernelNodeParams kscan = {};
+        kscan.func = (void*)k_gscan<Off>;
+        kscan.gridDim = dim3(sblocks);
+        kscan.blockDim = dim3(PT);
+        kscan.kernelParams = sargs;
+        cudaGraphNode_t n0, n1;
+        if (!ok(cudaGraphAddKernelNode(&n0, sp.conditional.phGraph_out[0], nullptr, 0, &kscan))) break;
+        void* pargs[] = {&G, &cc, &f0, &f1, &ctr};
+        cudaKernelNodeParams kproc = {};
+        kproc.func = (void*)k_gprocess<Off>;
+        kproc.gridDim = dim3(pblocks);
+        kproc.blockDim = dim3(PT);
+        kproc.kernelParams = pargs;
+        if (!ok(cudaGraphAddKernelNode(&n1, sp.conditional.phGraph_out[1], nullptr, 0, &kproc))) break;
+        if (!ok(cudaGraphInstantiate(&exec, top, 0))) break;
+        if (!ok(cudaGraphLaunch(exec, s))) break;
+    } while (false);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (top) cudaGraphDestroy(top);
+    return rc;
+}
+
+// Blocks per SM of the persistent form for options o on graph g whose
+// largest support is smax.  The automatic form takes 6 (throughput) when the
+// walk is large against the number of phases: when the shorter-row entries
+// all sub-levels walk (W = sum of min(d(u), d(v))) reach 2^24 per support
+// level, or 2^34 in all (at about 4.5e10 entries/s that is 0.4 s of walking,
+// far above the latency of a few thousand phases; large skewed graphs have
+// far fewer non-empty levels than their largest support).  Measured on
+// GB300: R-MAT scale 10 (W 1.6e5) and Chung-Lu 2^20 (W 1.8e9, 7.7e6 a
+// level) run fastest at 4 blocks per SM, the geometric graph 2^21 (3.3e7 a
+// level) and R-MAT scale 24 (W 2.7e11) at 6.
+inline int persistent_minb(const truss_graph* g, const truss_opts& o, int32_t smax) {
     if (o.loop == TRUSS_LOOP_PERSISTENT_LAT) return 4;
     if (o.loop == TRUSS_LOOP_PERSISTENT_OCC) return 6;
-    return g->max_deg <= 256 ? 6 : 4;
+    const int64_t per_level = g->dmin_sum / ((int64_t)(smax > 0 ? smax : 0) + 1);
+    return (per_level >= ((int64_t)1 << 24) || g->dmin_sum >= ((int64_t)1 << 34)) ? 6 : 4;
 }
 
 template <typename Off, int MINB>
@@ -1181,13 +1452,13 @@ int launch_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss
 
 template <typename Off>
 int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
-                   int64_t max_trace) {
-    if (persistent_minb(g, o) == 4) return launch_persistent<Off, 4>(g, o, s, d_trace, max_trace);
+                   int64_t max_trace, int32_t smax) {
+    if (persistent_minb(g, o, smax) == 4) return launch_persistent<Off, 4>(g, o, s, d_trace, max_trace);
     return launch_persistent<Off, 6>(g, o, s, d_trace, max_trace);
 }
 
 int check_opts(const truss_opts& o) {
-    if (o.loop < TRUSS_LOOP_PLAIN || o.loop > TRUSS_LOOP_PERSISTENT_OCC) return TRUSS_EINVAL;
+    if (o.loop < TRUSS_LOOP_PLAIN || o.loop > TRUSS_LOOP_GRAPH) return TRUSS_EINVAL;
     if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_LEARNED) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size)) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_trace) && (o.max_sub < 0 || !o.sync)) return TRUSS_EINVAL;
@@ -1205,12 +1476,20 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
     if (timed) CU(cudaEventRecord(ev[0], s));
     TRY(truss_support_internal(g, g->ss, s));
     unsigned long long* d_tri = reinterpret_cast<unsigned long long*>(g->ctr + C_TRI);
-    if (st) {
+    // the automatic persistent form needs the largest support on the host
+    // (it waits for the support phase); the other forms stay asynchronous
+    const bool pick = o.loop == TRUSS_LOOP_PERSISTENT;
+    int32_t smax = 0;
+    if (st || pick) {
         CU(cudaMemsetAsync(g->ctr + C_TRI, 0, 4 * sizeof(int), s));
         k_sum_support<<<grid_for(g->m, 256, (int64_t)g->sms * 4), 256, 0, s>>>(g->ss, g->m, d_tri, g->ctr + C_TRI + 2);
         CU(cudaGetLastError());
         truss_note_launch();
         CU(cudaMemcpyAsync(g->h_ctr + C_TRI, g->ctr + C_TRI, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (pick) {
+            CU(cudaStreamSynchronize(s));
+            smax = g->h_ctr[C_TRI + 2];
+        }
     }
     if (timed) CU(cudaEventRecord(ev[1], s));
     RunOut ro;
@@ -1222,7 +1501,10 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
     } else {
         truss_sublevel_trace* d_tr = nullptr;
         if (rec) CU(cudaMallocAsync((void**)&d_tr, sizeof(truss_sublevel_trace) * (size_t)o.max_sub, s));
-        rc = run_persistent<Off>(g, o, s, d_tr, rec ? o.max_sub : 0);
+        if (o.loop == TRUSS_LOOP_GRAPH)
+            rc = run_graph<Off>(g, o, s, d_tr, rec ? o.max_sub : 0);
+        else
+            rc = run_persistent<Off>(g, o, s, d_tr, rec ? o.max_sub : 0, smax);
         if (rc == TRUSS_OK && o.sync) {
             // the triangle words (C_TRI on) keep the support phase's count on
             // the host side; the peel cleared them on the device
@@ -1235,6 +1517,9 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             ro.nlevel = g->h_ctr[C_NLEVEL];
             ro.last_l = g->h_ctr[C_LAST_L];
             memcpy(&ro.scanned, g->h_ctr + C_SCANNED, sizeof(ro.scanned));
+            // the graph ran a control kernel per phase, a Scan or sub-level
+            // kernel in every phase but the last
+            if (o.loop == TRUSS_LOOP_GRAPH) truss_note_launch((int)(2 * (ro.nsub + ro.nscan) + 1));
             if (rec && rc == TRUSS_OK) {
                 const int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
                 CU(cudaMemcpyAsync(htr.data(), d_tr, sizeof(truss_sublevel_trace) * (size_t)k, cudaMemcpyDeviceToHost, s));
@@ -1286,6 +1571,7 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             unsigned long long tri = 0;
             memcpy(&tri, g->h_ctr + C_TRI, sizeof(tri));
             st->triangles = (int64_t)(tri / 3);
+            st->max_support = g->h_ctr[C_TRI + 2];
             // the last level that held edges is the final l minus one
             st->t_max = g->m > 0 ? ro.last_l - 1 + 2 : 0;
         }
@@ -1365,6 +1651,7 @@ int truss_ensure_workspace(truss_graph* g) {
         CU(cudaMalloc((void**)&g->live[k], sizeof(int32_t) * m));
     }
     CU(cudaMalloc((void**)&g->ctr, sizeof(int) * C_TOTAL));
+    CU(cudaMalloc(&g->gctl, sizeof(GCtl)));
     CU(cudaMallocHost((void**)&g->h_ctr, sizeof(int) * C_TOTAL));
     // chunk owner maps: enough for any sub-level of graphs up to moderate
     // size; larger chunk totals fall back to a search
@@ -1397,6 +1684,7 @@ void truss_release_workspace(truss_graph* g) {
         g->live[k] = nullptr;
     }
     cudaFree(g->ctr);
+    cudaFree(g->gctl);
     cudaFreeHost(g->h_ctr);
     for (int k = 0; k < 2; k++) {
         cudaFree(g->owner[k]);
@@ -1405,6 +1693,7 @@ void truss_release_workspace(truss_graph* g) {
     g->ss = nullptr;
     g->dmin = nullptr;
     g->ctr = nullptr;
+    g->gctl = nullptr;
     g->h_ctr = nullptr;
 }
 

@@ -87,7 +87,10 @@ def test_rmat24_sampled_certificate(pkt):
     G = pkt.build_csr(src, dst, g.n, offsets64=True)
     del src, dst
     step = torch.empty(G.m, dtype=torch.int32, device="cuda")
-    tau = G.decompose(loop=pkt.LOOP_PERSISTENT, peel_step=step).cpu().numpy()
+    tau, st = G.decompose(loop=pkt.LOOP_PERSISTENT, peel_step=step, stats=True)
+    # the walk holds over 2^34 shorter-row entries: the 6-blocks-per-SM form
+    assert st["dmin_sum"] >= 1 << 34 and st["blocks_per_sm"] == 6
+    tau = tau.cpu().numpy()
     step = step.cpu().numpy()
     u, v = G.edge_list()
     u, v = u.cpu().numpy(), v.cpu().numpy()

@@ -101,14 +101,14 @@ def test_edge_list_and_support(pkt, name, g, relabel, off64):
 # ------------------------------------------------------------ decomposition
 
 # the persistent kernel in both register budgets (the automatic choice picks
-# one of them per graph)
-LOOPS = ["plain", "persistent_lat", "persistent_occ"]
+# one of them per graph) and the graph-driven loop
+LOOPS = ["plain", "persistent_lat", "persistent_occ", "graph"]
 VARIANTS = ["auto", "thread", "group", "warp"]
 
 
 def _loop(pkt, name):
     return {"plain": pkt.LOOP_PLAIN, "persistent": pkt.LOOP_PERSISTENT, "persistent_lat": pkt.LOOP_PERSISTENT_LAT,
-            "persistent_occ": pkt.LOOP_PERSISTENT_OCC}[name]
+            "persistent_occ": pkt.LOOP_PERSISTENT_OCC, "graph": pkt.LOOP_GRAPH}[name]
 
 
 def _var(pkt, name):
@@ -288,16 +288,18 @@ def test_bad_ids_are_rejected(pkt):
     assert ex.value.status == pkt.EBADGRAPH
 
 
-def test_barrier_wait_limit_returns_status(pkt):
-    """A grid-barrier wait that runs past its limit ends the kernel with
-    TRUSS_ETIMEOUT (here the limit is 1 ns, so the first wait runs out); the
-    context stays usable and the next call is exact."""
+@pytest.mark.parametrize("loop", ["persistent_lat", "persistent_occ", "graph"])
+def test_barrier_wait_limit_returns_status(pkt, loop):
+    """A grid-barrier wait (persistent forms) or a phase (graph form) that
+    runs past its limit ends the run with TRUSS_ETIMEOUT (here the limit is
+    1 ns, so the first one runs out); the context stays usable and the next
+    call is exact."""
     g = gg.workload("rmat10_ef8")
     G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
     with pytest.raises(pkt.TrussError) as ex:
-        G.decompose(loop=pkt.LOOP_PERSISTENT, timeout_ns=1)
+        G.decompose(loop=_loop(pkt, loop), timeout_ns=1)
     assert ex.value.status == pkt.ETIMEOUT
-    tau = G.decompose(loop=pkt.LOOP_PERSISTENT)
+    tau = G.decompose(loop=_loop(pkt, loop))
     assert np.array_equal(host(tau), oracle.truss_of_edges(g.n, g.src, g.dst)[2])
 
 
@@ -343,23 +345,37 @@ def _scan_sequence(m, tau, step):
     return seq, visited
 
 
+def _want_bps(st):
+    per_level = st["dmin_sum"] // (st["max_support"] + 1)
+    return 6 if per_level >= 1 << 24 or st["dmin_sum"] >= 1 << 34 else 4
+
+
 def test_persistent_form_choice(pkt):
-    """The automatic persistent form takes 6 blocks per SM for graphs whose
-    rows are all short and 4 otherwise; forced forms are honoured; every
-    form gives the oracle's trussness."""
+    """The automatic persistent form takes 6 blocks per SM when the
+    shorter-row entries of the walk (W = sum of min(d(u), d(v))) reach 2^24
+    per support level or 2^34 in all, and 4 otherwise; forced forms are
+    honoured and every form gives the oracle's trussness."""
     import torch
 
-    for g, want_bps in ((gg.rgg2d(30000, 20.0, seed=5), 6), (gg.chung_lu(30000, 2.1, 12.0, 3000.0, seed=6), 4)):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for g in (gg.rgg2d(30000, 20.0, seed=5), gg.chung_lu(30000, 2.1, 12.0, 3000.0, seed=6)):
         G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
-        want = oracle.truss_of_edges(g.n, g.src, g.dst)[2]
-        for loop, bps in ((pkt.LOOP_PERSISTENT, want_bps), (pkt.LOOP_PERSISTENT_LAT, 4),
-                          (pkt.LOOP_PERSISTENT_OCC, 6)):
+        eu, ev, want = oracle.truss_of_edges(g.n, g.src, g.dst)
+        S = oracle.support(g.n, eu, ev)
+        for loop in (pkt.LOOP_PERSISTENT, pkt.LOOP_PERSISTENT_LAT, pkt.LOOP_PERSISTENT_OCC):
             tau, st = G.decompose(loop=loop, stats=True)
             assert np.array_equal(host(tau), want)
-            assert st["blocks_per_sm"] == bps
-            assert st["grid_blocks"] == bps * torch.cuda.get_device_properties(0).multi_processor_count
+            assert st["max_support"] == int(S.max())
+            bps = {pkt.LOOP_PERSISTENT: _want_bps(st), pkt.LOOP_PERSISTENT_LAT: 4, pkt.LOOP_PERSISTENT_OCC: 6}[loop]
+            assert st["blocks_per_sm"] == bps and st["grid_blocks"] == bps * sms
         _, st = G.decompose(loop=pkt.LOOP_PLAIN, stats=True)
         assert st["grid_blocks"] == 0 and st["blocks_per_sm"] == 0
+    # a level of the geometric workload holds about 3e7 entries: 6 blocks
+    g = gg.workload("rgg2d_n2^21_d32")
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    _, st = G.decompose(loop=pkt.LOOP_PERSISTENT, stats=True)
+    assert _want_bps(st) == 6 and st["blocks_per_sm"] == 6
+    G.free()
 
 
 @pytest.mark.parametrize("loop", LOOPS)
