@@ -315,6 +315,12 @@ def run_gpu(args):
                      "scans": st0["scans"], "scanned_entries": st0["scanned"]}
     if calib is not None:
         res["config"]["scheduler_calibration"] = calib
+    # the paper's own rate: wedges |^| = sum_v d(v)(d(v)-1)/2 per second
+    rowptr = G.csr()[0].to(torch.int64)
+    deg = rowptr[1:] - rowptr[:-1]
+    wedges = int((deg * (deg - 1) // 2).sum().item())
+    res["config"]["wedges"] = wedges
+    res["config"]["gweps"] = wedges / (total_ms / args.steps / 1000.0) / 1e9
     res["gpu_launches"] = int(sum(s["launches"] for s in stats))
     res["clocks"] = clk.summary()
 
