@@ -35,6 +35,7 @@
 
 // Support-kernel split: vertices whose upper degree d+(u) exceeds this are
 // handled by the block-per-vertex kernel instead of warp-per-vertex.
+#define TRUSS_SUP_SPLIT 128
 #define TRUSS_SUP_WARP_CAP 256
 #define TRUSS_SUP_BLOCK_CAP 12288
 

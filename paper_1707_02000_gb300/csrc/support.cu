@@ -11,7 +11,12 @@
 //
 // GB300 mapping:
 //  - warp per vertex (d+(u) <= TRUSS_SUP_WARP_CAP): N+(u) is staged in shared
-//    memory with a counter per entry and the prefix of d+(v) over v in N+(u);
+//    memory with a counter per entry, the start of each N+(v) and the prefix
+//    of d+(v) over v in N+(u).  Two instances of different capacity: when
+//    no N+(u) exceeds 128 entries, the 128-entry one (16 KB of shared memory
+//    a block, so 8 blocks of 8 warps fit an SM: a quarter less support time
+//    on the geometric workload than the 256-entry one at 6 blocks an SM);
+//    else the 256-entry one;
 //    the 32 lanes then walk the concatenation of all N+(v) lists as one flat
 //    range (balanced within the warp, coalesced reads of each N+(v)), and
 //    probe each w by binary search in the staged N+(u);
@@ -28,7 +33,7 @@
 namespace {
 
 constexpr int SW_WARPS = 8;  // warps per block, warp-per-vertex kernel
-constexpr int SW_CAP = TRUSS_SUP_WARP_CAP;
+constexpr int SW_SPLIT = TRUSS_SUP_SPLIT;  // rows up to here go to the smaller instance
 
 // S(e) lives in ss[e].x; the int view puts it at index 2e.
 __device__ __forceinline__ void add_support(int* S2, int32_t e, int v) { atomicAdd(S2 + 2 * (int64_t)e, v); }
@@ -52,22 +57,25 @@ __device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, in
     return lo;
 }
 
-template <typename Off>
+// Vertices u with d+(u) <= CAP (longer rows go to the block kernels).
+template <typename Off, int CAP>
 __global__ void __launch_bounds__(SW_WARPS * 32)
     k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                    const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S2) {
-    __shared__ int sK[SW_WARPS][SW_CAP];
-    __shared__ int sC[SW_WARPS][SW_CAP];
-    __shared__ int sP[SW_WARPS][SW_CAP + 1];
+    __shared__ int sK[SW_WARPS][CAP];
+    __shared__ int sC[SW_WARPS][CAP];
+    __shared__ int sP[SW_WARPS][CAP + 1];
+    __shared__ Off sE[SW_WARPS][CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* K = sK[warp];
     int* C = sC[warp];
     int* P = sP[warp];
+    Off* E = sE[warp];
     const int64_t nwarps = (int64_t)gridDim.x * SW_WARPS;
     for (int64_t u = blockIdx.x * (int64_t)SW_WARPS + warp; u < n; u += nwarps) {
         const Off up0 = eo[u], up1 = rowptr[u + 1];
         const int d = (int)(up1 - up0);
-        if (d < 2 || d > SW_CAP) continue;  // no triangle at u / handled by the block kernels
+        if (d < 2 || d > CAP) continue;  // no triangle at u / handled by the block kernels
         // stage N+(u), zero counters, prefix of d+(v)
         int carry = 0;
         for (int b = 0; b < d; b += 32) {
@@ -77,7 +85,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
                 int v = __ldg(col + up0 + p);
                 K[p] = v;
                 C[p] = 0;
-                dv = (int)(__ldg(rowptr + v + 1) - __ldg(eo + v));
+                const Off v0 = __ldg(eo + v);
+                E[p] = v0;
+                dv = (int)(__ldg(rowptr + v + 1) - v0);
             }
             int x = dv;
 #pragma unroll
@@ -91,16 +101,27 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
         if (lane == 0) P[d] = carry;
         __syncwarp();
         const int total = carry;
-        for (int idx = lane; idx < total; idx += 32) {
-            int p = seg_of(P, d, idx);
-            int v = K[p];
-            Off q = __ldg(eo + v) + (idx - P[p]);
-            int w = __ldg(col + q);
-            int r = lower_bound_smem(K, p + 1, d, w);
-            if (r < d && K[r] == w) {
-                atomicAdd(&C[r], 1);  // edge {u, w}
-                atomicAdd(&C[p], 1);  // edge {u, v}
-                add_support(S2, __ldg(eid + q), 1);  // edge {v, w}
+        // two entries per lane (idx and idx + 32) with independent chains
+        for (int idx = lane; idx < total; idx += 64) {
+            const int i2 = idx + 32;
+            const bool two = i2 < total;
+            const int p1 = seg_of(P, d, idx);
+            const int p2 = two ? seg_of(P, d, i2) : p1;
+            const Off q1 = E[p1] + (idx - P[p1]);  // N+(v) starts at E[p] (staged)
+            const Off q2 = two ? E[p2] + (i2 - P[p2]) : q1;
+            const int w1 = __ldg(col + q1), x1 = __ldg(eid + q1);
+            const int w2 = __ldg(col + q2), x2 = __ldg(eid + q2);
+            const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
+            const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
+            if (r1 < d && K[r1] == w1) {
+                atomicAdd(&C[r1], 1);  // edge {u, w}
+                atomicAdd(&C[p1], 1);  // edge {u, v}
+                add_support(S2, x1, 1);  // edge {v, w}
+            }
+            if (two && r2 < d && K[r2] == w2) {
+                atomicAdd(&C[r2], 1);
+                atomicAdd(&C[p2], 1);
+                add_support(S2, x2, 1);
             }
         }
         __syncwarp();
@@ -237,8 +258,15 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     CU(cudaGetLastError());
     truss_note_launch();
     if (g->n > 0 && g->m > 0) {
+        // one warp-per-vertex instance: the 128-entry one when no N+(u) is
+        // longer (8 blocks an SM), else the 256-entry one (6 blocks an SM);
+        // two instances run one after the other cost more than either
         int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
-        k_support_warp<Off><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
+        if (g->max_updeg <= SW_SPLIT)
+            k_support_warp<Off, SW_SPLIT><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
+        else
+            k_support_warp<Off, TRUSS_SUP_WARP_CAP>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
         CU(cudaGetLastError());
         truss_note_launch();
     }
