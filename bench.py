@@ -54,6 +54,21 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def whole_job(total_ms: float, units_per_step: int, steps: int, dist=None, device="cpu"):
+    """Whole-job throughput of a replicas run: the slowest rank's time
+    (max over ranks of each rank's summed step times, ms) and the units all
+    ranks processed over it.  Returns (value per second, max total ms)."""
+    import torch
+
+    ws = 1
+    if dist is not None and dist.is_initialized():
+        ws = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return units_per_step * steps * ws / (total_ms / 1000.0), total_ms
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -298,12 +313,7 @@ def run_gpu(args):
 
     with ClockSampler(local) as clk:
         per, stats = timed(loop, variant, args.steps, args.warmup, params)
-    total_ms = sum(per)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = m * args.steps * ws / (total_ms / 1000.0)
+    value, total_ms = whole_job(sum(per), m, args.steps, dist, device="cuda")
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
