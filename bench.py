@@ -226,7 +226,7 @@ CALIB_SEEDS = (101, 102)
 VARIANTS = {}
 VARIANT_DESC = {"learned": "learned cost model per sub-level (heuristic below 64 light edges)",
                 "heuristic": "fixed per-sub-level heuristic", "thread": "thread per light edge",
-                "group": "8 lanes per light edge", "warp": "warp per light edge"}
+                "group": "half a warp per light edge", "warp": "warp per light edge"}
 
 
 def calibrate(pkt, workload, seeds, repeats=2, epochs=2000):

@@ -158,7 +158,10 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
  * lanes walk each of the other ("light") edges. */
 #define TRUSS_VAR_AUTO (-1)   /* chosen per sub-level from the frontier size */
 #define TRUSS_VAR_THREAD 0    /* one thread per light edge                   */
-#define TRUSS_VAR_GROUP 1     /* eight lanes per light edge                  */
+#define TRUSS_VAR_GROUP 1     /* half a warp (16 lanes) per light edge; a
+                                 longer row of at most 64 entries is held in
+                                 registers and searched by shuffles; the
+                                 default                                     */
 #define TRUSS_VAR_WARP 2      /* one warp per light edge                     */
 #define TRUSS_VAR_LEARNED 3   /* chosen per sub-level by the learned cost
                                  model (opts->sched_params); falls back to
@@ -185,7 +188,7 @@ TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 /* One record per non-empty sub-level (see truss_opts.h_trace). */
 typedef struct truss_sublevel_trace {
     int32_t level;     /* support level l                                     */
-    int32_t group;     /* lanes per light edge used (1, 8 or 32)              */
+    int32_t group;     /* lanes per light edge used (1, 16 or 32)             */
     int32_t n_light;   /* frontier edges with shorter row <= 32 entries       */
     int32_t n_heavy;   /* the other frontier edges                            */
     uint32_t n_chunks; /* heavy-row chunks shared out to warps                */

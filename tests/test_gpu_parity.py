@@ -423,7 +423,7 @@ def test_sublevel_trace(pkt, loop):
     assert np.array_equal(host(tau), want)
     assert np.array_equal(tr["level"], olv) and np.array_equal(tr["n_light"] + tr["n_heavy"], osz)
     assert np.array_equal(tr["todo"], eu.size - np.concatenate([[0], np.cumsum(osz)[:-1]]))
-    assert set(np.unique(tr["group"])) <= {1, 8, 32}
+    assert set(np.unique(tr["group"])) <= {1, 16, 32}
     assert np.all(tr["t_ns"] > 0) and tr["scan_ns"][0] > 0 and np.all(tr["scan_ns"] >= 0)
     deg = np.bincount(np.concatenate([eu, ev]), minlength=g.n)
     dmin = np.minimum(deg[eu], deg[ev])

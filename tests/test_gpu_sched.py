@@ -93,7 +93,7 @@ def test_learned_and_autotuned_schedules_are_exact(pkt):
         pkt.sched_train(p, _dev(x), _dev(y), epochs=300)
         tau, tr = G.decompose(variant=pkt.VAR_LEARNED, sched_params=p, trace=True)
         assert np.array_equal(tau.cpu().numpy(), want)
-        assert set(np.unique(tr["group"])) <= {1, 8, 32}
+        assert set(np.unique(tr["group"])) <= {1, 16, 32}
         table = G.autotune()
         assert table.shape == (pkt.TUNE_CLASSES,) and set(np.unique(table)) <= {-1, 0, 1, 2}
         tau = G.decompose(variant=pkt.VAR_AUTO, tune_table=table)
@@ -105,9 +105,9 @@ def test_learned_choice_regret_on_held_out_sublevels(pkt):
     """Train on sub-levels of two graphs; on a held-out graph of each family,
     every sub-level's time under each variant is measured, and the model's
     choices are scored by regret (time above the per-sub-level best).  The
-    trained model must do better than its untrained start and no worse than
-    the worst fixed variant; the gain over the default (a warp per light
-    edge) is printed."""
+    trained model must do better than its untrained start, no worse than the
+    worst fixed variant, and (within timing noise) no worse than the default
+    mapping; the regrets are printed."""
     import torch
 
     train = [gg.rgg2d(1 << 18, 32.0, seed=51), gg.chung_lu(1 << 18, 2.1, 20.0, 4096.0, seed=52)]
@@ -144,4 +144,7 @@ def test_learned_choice_regret_on_held_out_sublevels(pkt):
           f"{[round(r / 1e6, 3) for r in r_fixed]}")
     assert r_learned <= max(r_fixed)
     assert r_learned <= r_untrained + 1e-9 or r_untrained == 0
+    # against the method without it (the default mapping, half a warp per
+    # light edge), allowing 2 % of the best total for timing noise
+    assert r_learned <= r_fixed[1] + 0.02 * best, (r_learned, r_fixed)
     torch.cuda.synchronize()
