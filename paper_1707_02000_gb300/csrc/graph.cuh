@@ -26,7 +26,7 @@
 //                     heavy edges, first chunk number of each heavy edge
 //   live[2] int32[m]  edges each Scan found above its level: the only edges
 //                     the next Scan visits (a list that shrinks level by level)
-//   owner[2] uint32   chunk -> heavy-list position for each frontier side
+//   owner[2] int2     chunk -> {edge, chunk index in its row}, each side
 //   ctr    int[...]   device counters (see peel.cu)
 #pragma once
 #include "common.cuh"
@@ -60,6 +60,7 @@ struct truss_graph {
     int64_t max_deg = 0;
     int last_grid = 0, last_per_sm = 0;  // blocks of the last persistent launch
     void* gctl = nullptr;   // state of the graph-driven level loop
+    void* rows = nullptr;   // per edge: shorter row bounds, longer row bounds (Off x 4)
     int64_t max_updeg = 0;
     int64_t wedges_up = 0;  // sum_v d-(v) d+(v)
     int64_t dmin_sum = 0;   // sum_e min(d(u), d(v))
@@ -69,7 +70,7 @@ struct truss_graph {
     int32_t* dmin = nullptr;
     int32_t* fq[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int32_t* live[2] = {nullptr, nullptr};  // live-edge lists of consecutive Scans
-    uint32_t* owner[2] = {nullptr, nullptr}; // chunk -> heavy-list position, per side
+    int2* owner[2] = {nullptr, nullptr};     // chunk -> {edge, chunk index in its row}, per side
     uint32_t ocap = 0;
     int* ctr = nullptr;
     int* h_ctr = nullptr;  // pinned host mirror

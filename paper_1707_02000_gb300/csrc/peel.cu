@@ -67,7 +67,7 @@ struct Frontier {
     int32_t* light;
     int32_t* heavy;
     uint32_t* cbase;  // first chunk number of each heavy edge (monotone)
-    uint32_t* owner;  // heavy-list position owning each chunk (if the total fits ocap)
+    int2* owner;      // per chunk: {owning edge, chunk index within its row} (if the total fits ocap)
 };
 
 struct PeelSmem {
@@ -128,6 +128,7 @@ struct Graph {
     const int32_t* __restrict__ eid;
     const int2* __restrict__ el;
     const int32_t* __restrict__ dmin;  // min(d(u), d(v)) per edge
+    const Off* __restrict__ rows;      // per edge: shorter row [a0, a1), longer row [b0, b1)
     int2* ss;
     int64_t m;
     int hc;  // heavy chunk length (entries of the shorter row)
@@ -136,10 +137,12 @@ struct Graph {
 
 __device__ __forceinline__ uint32_t nchunks_of(int d, int hc) { return (uint32_t)((d + hc - 1) / hc); }
 
-// owner[base .. base + n) = q when that range fits the map
-__device__ __forceinline__ void write_owner(const Frontier& out, uint32_t ocap, uint32_t base, uint32_t n, int q) {
+// owner[base + k] = {f, k} for the n chunks of heavy edge f, when that
+// range fits the map
+__device__ __forceinline__ void write_owner(const Frontier& out, uint32_t ocap, uint32_t base, uint32_t n,
+                                            int32_t f) {
     if ((uint64_t)base + n <= ocap)
-        for (uint32_t k = 0; k < n; k++) out.owner[base + k] = (uint32_t)q;
+        for (uint32_t k = 0; k < n; k++) out.owner[base + k] = make_int2(f, (int)k);
 }
 
 // Next-frontier appends of one block during a sub-level: staged in shared
@@ -177,7 +180,7 @@ struct Appender {
             const int q = (int)(old >> 32);
             out.heavy[q] = f;
             out.cbase[q] = (uint32_t)old;
-            write_owner(out, ocap, (uint32_t)old, nch, q);
+            write_owner(out, ocap, (uint32_t)old, nch, f);
         }
     }
     // whole block; leaves the stage empty
@@ -232,7 +235,7 @@ struct Appender {
             if (i < kh) {
                 out.heavy[sm->hq0 + i] = sm->hbuf[i];
                 out.cbase[sm->hq0 + i] = pc;
-                write_owner(out, ocap, pc, c[k], sm->hq0 + i);
+                write_owner(out, ocap, pc, c[k], sm->hbuf[i]);
                 pc += c[k];
             }
         }
@@ -310,13 +313,18 @@ struct Rows {
     Off a0, a1, b0, b1;  // shorter row [a0, a1), longer row [b0, b1)
 };
 
+// The rows of edge e from its precomputed record (one 16-byte load for
+// int32 offsets, two for int64): no endpoint -> row-pointer round trip.
 template <typename Off>
 __device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
-    const int2 uv = __ldg(G.el + e);
-    const Off u0 = __ldg(G.rowptr + uv.x), u1 = __ldg(G.rowptr + uv.x + 1);
-    const Off v0 = __ldg(G.rowptr + uv.y), v1 = __ldg(G.rowptr + uv.y + 1);
-    if (u1 - u0 <= v1 - v0) return Rows<Off>{u0, u1, v0, v1};
-    return Rows<Off>{v0, v1, u0, u1};
+    if constexpr (sizeof(Off) == 4) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(G.rows) + e);
+        return Rows<Off>{v.x, v.y, v.z, v.w};
+    } else {
+        const longlong2* p = reinterpret_cast<const longlong2*>(G.rows) + 2 * (int64_t)e;
+        const longlong2 a = __ldg(p), b = __ldg(p + 1);
+        return Rows<Off>{a.x, a.y, b.x, b.y};
+    }
 }
 
 // Slots of k1 and k2 in the ascending row a[lo, lo + n) (n >= 1), or -1.
@@ -509,13 +517,31 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
                 walk_rows<Off>(G, e1, r.a0, r.a1, r, sub, gsz, l, g, ap);
         }
     }
-    // heavy chunks: warp w takes the contiguous chunk range [c0, c1), so it
-    // looks up the owning edge once and then walks forward through the list
+    // heavy chunks: warp w takes the contiguous chunk range [c0, c1).  With
+    // the owner map, one load gives a chunk's edge and its place in the row
+    // (the next chunk's entry is fetched during the current walk); without
+    // it, the owning edge is found once by search and the warp walks forward
+    // through the list.
     const int lane = threadIdx.x & 31;
     const uint64_t nw = (uint64_t)(nth / 32), w = (uint64_t)(gtid / 32);
     const uint32_t c0 = (uint32_t)((uint64_t)nchunk * w / nw), c1 = (uint32_t)((uint64_t)nchunk * (w + 1) / nw);
-    if (c0 < c1) {
-        int q = nchunk <= G.ocap ? (int)__ldcg(cur.owner + c0) : chunk_owner(cur.cbase, nh, c0);
+    if (c0 < c1 && nchunk <= G.ocap) {
+        int2 o = __ldcg(cur.owner + c0);
+        int32_t e1 = o.x;
+        Rows<Off> r = rows_of<Off>(G, e1);
+        for (uint32_t c = c0; c < c1; c++) {
+            const int2 on = c + 1 < c1 ? __ldcg(cur.owner + c + 1) : o;
+            const int64_t s0 = (int64_t)r.a0 + (int64_t)o.y * G.hc;
+            const int64_t s1 = min((int64_t)r.a1, s0 + (int64_t)G.hc);
+            walk_warp<Off>(G, e1, (Off)s0, (Off)s1, r, lane, l, g, ap);
+            if (on.x != e1) {
+                e1 = on.x;
+                r = rows_of<Off>(G, e1);
+            }
+            o = on;
+        }
+    } else if (c0 < c1) {
+        int q = chunk_owner(cur.cbase, nh, c0);
         uint32_t qb = __ldcg(cur.cbase + q);
         uint32_t qn = q + 1 < nh ? __ldcg(cur.cbase + q + 1) : nchunk;
         int32_t e1 = __ldcg(cur.heavy + q);
@@ -613,7 +639,7 @@ __device__ __forceinline__ void warp_classify_append(bool hit, int32_t e, const 
             const int q = (int)(old >> 32) + __popc(b & lanemask_lt());
             out.heavy[q] = e;
             out.cbase[q] = (uint32_t)old + x - c;
-            write_owner(out, ocap, (uint32_t)old + x - c, c, q);
+            write_owner(out, ocap, (uint32_t)old + x - c, c, e);
         }
     }
 }
@@ -745,7 +771,7 @@ __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* ke
                 } else {
                     out.heavy[ph] = e[k];
                     out.cbase[ph] = pc;
-                    write_owner(out, ocap, pc, c[k], ph);
+                    write_owner(out, ocap, pc, c[k], e[k]);
                     ph++;
                     pc += c[k];
                 }
@@ -1071,11 +1097,18 @@ __global__ void k_map_ids(const int32_t* __restrict__ in, int64_t k, const int32
 }
 
 template <typename Off>
-__global__ void k_dmin(const Off* __restrict__ rowptr, const int2* __restrict__ el, int64_t m, int32_t* __restrict__ dmin) {
+__global__ void k_dmin(const Off* __restrict__ rowptr, const int2* __restrict__ el, int64_t m, int32_t* __restrict__ dmin,
+                       Off* __restrict__ rows) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         int2 xy = el[e];
-        int64_t du = (int64_t)(rowptr[xy.x + 1] - rowptr[xy.x]), dv = (int64_t)(rowptr[xy.y + 1] - rowptr[xy.y]);
-        dmin[e] = (int32_t)min(du, dv);
+        const Off u0 = rowptr[xy.x], u1 = rowptr[xy.x + 1], v0 = rowptr[xy.y], v1 = rowptr[xy.y + 1];
+        const bool ushort = u1 - u0 <= v1 - v0;
+        dmin[e] = (int32_t)(ushort ? u1 - u0 : v1 - v0);
+        Off* r = rows + 4 * e;
+        r[0] = ushort ? u0 : v0;
+        r[1] = ushort ? u1 : v1;
+        r[2] = ushort ? v0 : u0;
+        r[3] = ushort ? v1 : u1;
     }
 }
 
@@ -1090,7 +1123,8 @@ int process_blocks(const truss_graph* g) {
 
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
-    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, g->ss, g->m, g->hc, g->ocap};
+    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, (const Off*)g->rows, g->ss, g->m, g->hc,
+                      g->ocap};
 }
 
 TuneTable tune_table_of(const truss_opts& o) {
@@ -1702,6 +1736,7 @@ int truss_ensure_workspace(truss_graph* g) {
     g->hc = (int)hc;
     CU(cudaMalloc((void**)&g->ss, sizeof(int2) * (m + 1)));
     CU(cudaMalloc((void**)&g->dmin, sizeof(int32_t) * m));
+    CU(cudaMalloc(&g->rows, (g->off64 ? sizeof(int64_t) : sizeof(int32_t)) * 4 * m));
     for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) CU(cudaMalloc((void**)&g->fq[k][j], sizeof(int32_t) * m));
         CU(cudaMalloc((void**)&g->live[k], sizeof(int32_t) * m));
@@ -1715,13 +1750,15 @@ int truss_ensure_workspace(truss_graph* g) {
         const int64_t want = (int64_t)g->m + g->dmin_sum / hc + 1;
         const int64_t cap = std::min<int64_t>(want, std::min<int64_t>(4 * (int64_t)g->m + 1024, (int64_t)UINT32_MAX));
         g->ocap = (uint32_t)cap;
-        for (int k = 0; k < 2; k++) CU(cudaMalloc((void**)&g->owner[k], sizeof(uint32_t) * (size_t)cap));
+        for (int k = 0; k < 2; k++) CU(cudaMalloc((void**)&g->owner[k], sizeof(int2) * (size_t)cap));
     }
     if (g->m > 0) {
         if (g->off64)
-            k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin);
+            k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin,
+                                                           (int64_t*)g->rows);
         else
-            k_dmin<int32_t><<<grid_for(g->m, 256), 256>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin);
+            k_dmin<int32_t><<<grid_for(g->m, 256), 256>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin,
+                                                           (int32_t*)g->rows);
         CU(cudaGetLastError());
         CU(cudaDeviceSynchronize());
     }
@@ -1731,6 +1768,8 @@ int truss_ensure_workspace(truss_graph* g) {
 void truss_release_workspace(truss_graph* g) {
     cudaFree(g->ss);
     cudaFree(g->dmin);
+    cudaFree(g->rows);
+    g->rows = nullptr;
     for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) {
             cudaFree(g->fq[k][j]);
