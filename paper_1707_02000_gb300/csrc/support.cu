@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
     }
 }
 
-constexpr int SB_THREADS = 512;
+constexpr int SB_THREADS = 1024;  // one block an SM (shared memory); 512 left it latency-bound
 
 // Block-wide inclusive scan helper for the prefix of d+(v).
 __device__ int block_scan_incl(int x, int* wsum) {
@@ -195,16 +195,27 @@ __global__ void __launch_bounds__(SB_THREADS)
         const int total = s_carry;
         if (threadIdx.x == 0) P[d] = total;
         __syncthreads();
-        for (int idx = threadIdx.x; idx < total; idx += SB_THREADS) {
-            int p = seg_of(P, d, idx);
-            int v = K[p];
-            Off q = __ldg(eo + v) + (idx - P[p]);
-            int w = __ldg(col + q);
-            int r = lower_bound_smem(K, p + 1, d, w);
-            if (r < d && K[r] == w) {
-                atomicAdd(&C[r], 1);
-                atomicAdd(&C[p], 1);
-                add_support(S2, __ldg(eid + q), 1);
+        // two probes per thread (idx and idx + SB_THREADS), independent chains
+        for (int idx = threadIdx.x; idx < total; idx += 2 * SB_THREADS) {
+            const int i2 = idx + SB_THREADS;
+            const bool two = i2 < total;
+            const int p1 = seg_of(P, d, idx);
+            const int p2 = two ? seg_of(P, d, i2) : p1;
+            const Off q1 = __ldg(eo + K[p1]) + (idx - P[p1]);
+            const Off q2 = two ? __ldg(eo + K[p2]) + (i2 - P[p2]) : q1;
+            const int w1 = __ldg(col + q1), x1 = __ldg(eid + q1);
+            const int w2 = __ldg(col + q2), x2 = __ldg(eid + q2);
+            const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
+            const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
+            if (r1 < d && K[r1] == w1) {
+                atomicAdd(&C[r1], 1);
+                atomicAdd(&C[p1], 1);
+                add_support(S2, x1, 1);
+            }
+            if (two && r2 < d && K[r2] == w2) {
+                atomicAdd(&C[r2], 1);
+                atomicAdd(&C[p2], 1);
+                add_support(S2, x2, 1);
             }
         }
         __syncthreads();
