@@ -61,6 +61,12 @@ struct truss_graph {
     int last_grid = 0, last_per_sm = 0;  // blocks of the last persistent launch
     void* gctl = nullptr;   // state of the graph-driven level loop
     void* rows = nullptr;   // per edge: shorter row bounds, longer row bounds (Off x 4)
+    int32_t* lhub = nullptr;     // per edge: hub index of the longer row's vertex, -1 if none
+    int32_t* hub_of = nullptr;   // per vertex: hub index, -1 if none
+    unsigned long long* hub_bits = nullptr;  // per hub: neighbour bitmap (hub_words words)
+    uint32_t* hub_pre = nullptr; // per hub: neighbours before each 512-bit block
+    int32_t n_hub = 0;
+    int64_t hub_words = 0;
     int64_t max_updeg = 0;
     int64_t wedges_up = 0;  // sum_v d-(v) d+(v)
     int64_t dmin_sum = 0;   // sum_e min(d(u), d(v))

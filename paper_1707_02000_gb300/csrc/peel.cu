@@ -129,6 +129,10 @@ struct Graph {
     const int2* __restrict__ el;
     const int32_t* __restrict__ dmin;  // min(d(u), d(v)) per edge
     const Off* __restrict__ rows;      // per edge: shorter row [a0, a1), longer row [b0, b1)
+    const int32_t* __restrict__ lhub;  // per edge: hub index of the longer row's vertex, -1 if none
+    const unsigned long long* __restrict__ hbits;  // per hub: neighbour bitmap, hw words
+    const uint32_t* __restrict__ hpre;             // per hub: neighbours before each 512-bit block
+    int64_t hw;                                    // words per hub bitmap (a multiple of 8)
     int2* ss;
     int64_t m;
     int hc;  // heavy chunk length (entries of the shorter row)
@@ -311,19 +315,21 @@ __device__ __forceinline__ void on_triangles(int2* ss, int32_t e1, bool ok1, int
 template <typename Off>
 struct Rows {
     Off a0, a1, b0, b1;  // shorter row [a0, a1), longer row [b0, b1)
+    int32_t hub;         // hub index of the longer row's vertex, -1 if none
 };
 
 // The rows of edge e from its precomputed record (one 16-byte load for
 // int32 offsets, two for int64): no endpoint -> row-pointer round trip.
 template <typename Off>
 __device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
+    const int32_t hub = __ldg(G.lhub + e);
     if constexpr (sizeof(Off) == 4) {
         const int4 v = __ldg(reinterpret_cast<const int4*>(G.rows) + e);
-        return Rows<Off>{v.x, v.y, v.z, v.w};
+        return Rows<Off>{v.x, v.y, v.z, v.w, hub};
     } else {
         const longlong2* p = reinterpret_cast<const longlong2*>(G.rows) + 2 * (int64_t)e;
         const longlong2 a = __ldg(p), b = __ldg(p + 1);
-        return Rows<Off>{a.x, a.y, b.x, b.y};
+        return Rows<Off>{a.x, a.y, b.x, b.y, hub};
     }
 }
 
@@ -353,6 +359,25 @@ __device__ __forceinline__ void find2(const int32_t* __restrict__ a, Off lo, Off
     p2 = v2 == k2 ? b2 : (Off)-1;
 }
 
+// Slot of w in the row (starting at slot b0) of the vertex that owns hub h,
+// or -1: the bit of w in the hub's neighbour bitmap, and its rank = the
+// neighbours before w's 512-bit block (stored) + those in the block's words
+// before w's word + those below w in its word.  All loads are independent
+// (one round trip; the block's words share a 64-byte line).
+template <typename Off>
+__device__ __forceinline__ Off hub_find(const Graph<Off>& G, int32_t h, Off b0, int32_t w) {
+    const unsigned long long* B = G.hbits + (int64_t)h * G.hw;
+    const int64_t wi = w >> 6, wb = wi & ~(int64_t)7;
+    const unsigned long long word = __ldg(B + wi);
+    uint32_t rank = __ldg(G.hpre + (int64_t)h * (G.hw >> 3) + (w >> 9));
+#pragma unroll
+    for (int k = 0; k < 7; k++)
+        if (wb + k < wi) rank += (uint32_t)__popcll(__ldg(B + wb + k));
+    const int bit = w & 63;
+    rank += (uint32_t)__popcll(word & ((1ull << bit) - 1ull));
+    return ((word >> bit) & 1ull) ? b0 + (Off)rank : (Off)-1;
+}
+
 // All triangles through e1 whose apex is one of the slots start, start+step,
 // ... of [a0, a1) (part of the shorter row), each probed in the longer row;
 // a lane takes two slots at a time (j and j + step) and searches for both
@@ -366,7 +391,12 @@ __device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a
         const int32_t w1 = __ldg(G.col + j), x1 = __ldg(G.eid + j);
         const int32_t w2 = two ? __ldg(G.col + j2) : w1, x2 = two ? __ldg(G.eid + j2) : x1;
         Off q1, q2;
-        find2<Off>(G.col, r.b0, r.b1 - r.b0, w1, w2, q1, q2);
+        if (r.hub >= 0) {
+            q1 = hub_find<Off>(G, r.hub, r.b0, w1);
+            q2 = hub_find<Off>(G, r.hub, r.b0, w2);
+        } else {
+            find2<Off>(G.col, r.b0, r.b1 - r.b0, w1, w2, q1, q2);
+        }
         const bool ok1 = q1 >= 0, ok2 = two && q2 >= 0;
         const int32_t y1 = ok1 ? __ldg(G.eid + q1) : 0, y2 = ok2 ? __ldg(G.eid + q2) : 0;
         on_triangles(G.ss, e1, ok1, x1, y1, ok2, x2, y2, l, g, ap);
@@ -498,7 +528,7 @@ __device__ void process_frontier(const Graph<Off>& G, const Frontier cur, int nl
             const int64_t i = 2 * pw + (lane >> 4);
             const bool valid = i < nl;
             const int32_t e1 = valid ? __ldcg(cur.light + i) : 0;
-            Rows<Off> r{0, 0, 0, 0};
+            Rows<Off> r{0, 0, 0, 0, -1};
             if (valid) r = rows_of<Off>(G, e1);
             if (__all_sync(FULL_MASK, !valid || r.b1 - r.b0 <= 64))
                 walk_half_reg<Off>(G, valid, e1, r, lane & 15, l, g, ap);
@@ -1098,17 +1128,96 @@ __global__ void k_map_ids(const int32_t* __restrict__ in, int64_t k, const int32
 
 template <typename Off>
 __global__ void k_dmin(const Off* __restrict__ rowptr, const int2* __restrict__ el, int64_t m, int32_t* __restrict__ dmin,
-                       Off* __restrict__ rows) {
+                       Off* __restrict__ rows, const int32_t* __restrict__ hub_of, int32_t* __restrict__ lhub) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         int2 xy = el[e];
         const Off u0 = rowptr[xy.x], u1 = rowptr[xy.x + 1], v0 = rowptr[xy.y], v1 = rowptr[xy.y + 1];
         const bool ushort = u1 - u0 <= v1 - v0;
         dmin[e] = (int32_t)(ushort ? u1 - u0 : v1 - v0);
+        lhub[e] = hub_of ? hub_of[ushort ? xy.y : xy.x] : -1;
         Off* r = rows + 4 * e;
         r[0] = ushort ? u0 : v0;
         r[1] = ushort ? u1 : v1;
         r[2] = ushort ? v0 : u0;
         r[3] = ushort ? v1 : u1;
+    }
+}
+
+// Hub bitmaps: for each vertex of degree >= the hub threshold, a bitmap
+// over vertex ids with its neighbours set and, per 512-bit block, the number
+// of neighbours before the block; ProcessSubLevel probes these rows through
+// hub_find instead of a binary search.
+template <typename Off>
+__global__ void k_count_deg(const Off* __restrict__ rowptr, int32_t n, int64_t thr, int* cnt) {
+    int c = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        c += (rowptr[v + 1] - rowptr[v]) >= thr;
+    c = warp_sum(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+template <typename Off>
+__global__ void k_hub_list(const Off* __restrict__ rowptr, int32_t n, int64_t thr, int32_t* __restrict__ hub_of,
+                           int32_t* __restrict__ hub_vert, int* cnt) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        int h = -1;
+        if (rowptr[v + 1] - rowptr[v] >= thr) {
+            h = atomicAdd(cnt, 1);
+            hub_vert[h] = (int32_t)v;
+        }
+        hub_of[v] = h;
+    }
+}
+
+template <typename Off>
+__global__ void k_hub_fill(const Off* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const int32_t* __restrict__ hub_vert, int32_t nhub, int64_t hw,
+                           unsigned long long* __restrict__ bits) {
+    for (int32_t h = blockIdx.x; h < nhub; h += gridDim.x) {
+        const int32_t v = hub_vert[h];
+        unsigned long long* B = bits + (int64_t)h * hw;
+        for (Off j = rowptr[v] + threadIdx.x; j < rowptr[v + 1]; j += blockDim.x) {
+            const int32_t w = col[j];
+            atomicOr(B + (w >> 6), 1ull << (w & 63));
+        }
+    }
+}
+
+// per hub: exclusive prefix over its 512-bit blocks of the neighbour counts
+__global__ void k_hub_pre(const unsigned long long* __restrict__ bits, int32_t nhub, int64_t hw,
+                          uint32_t* __restrict__ pre) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int64_t nb = hw >> 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int32_t h = blockIdx.x; h < nhub; h += gridDim.x) {
+        const unsigned long long* B = bits + (int64_t)h * hw;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (int64_t base = 0; base < nb; base += blockDim.x) {
+            const int64_t b = base + threadIdx.x;
+            uint32_t c = 0;
+            if (b < nb)
+                for (int k = 0; k < 8; k++) c += (uint32_t)__popcll(B[b * 8 + k]);
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            uint32_t before = carry;
+            for (int w2 = 0; w2 < warp; w2++) before += wsum[w2];
+            if (b < nb) pre[(int64_t)h * nb + b] = before + x - c;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t t = 0;
+                for (int w2 = 0; w2 < nwarp; w2++) t += wsum[w2];
+                carry += t;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -1123,8 +1232,8 @@ int process_blocks(const truss_graph* g) {
 
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
-    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, (const Off*)g->rows, g->ss, g->m, g->hc,
-                      g->ocap};
+    return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, (const Off*)g->rows, g->lhub,
+                      g->hub_bits, g->hub_pre, g->hub_words, g->ss, g->m, g->hc, g->ocap};
 }
 
 TuneTable tune_table_of(const truss_opts& o) {
@@ -1726,6 +1835,51 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 
 }  // namespace
 
+// Hub bitmaps for the vertices of degree >= thr, thr = 1024 doubled until
+// they fit a budget of 32 bytes per edge (at most 8 GiB): one bit per vertex
+// id plus 4 bytes per 512 ids for each hub.
+template <typename Off>
+int build_hubs(truss_graph* g) {
+    const Off* rowptr = (const Off*)g->rowptr;
+    const int64_t hw = (((int64_t)g->n + 511) / 512) * 8;
+    const int64_t per_hub = hw * 8 + (hw / 8) * 4;
+    const int64_t budget = std::min<int64_t>((int64_t)8 << 30, 32 * g->m);
+    int* d_cnt = nullptr;
+    CU(cudaMalloc((void**)&d_cnt, sizeof(int)));
+    int64_t thr = 1024;
+    int cnt = 0;
+    for (;;) {
+        CU(cudaMemset(d_cnt, 0, sizeof(int)));
+        k_count_deg<Off><<<grid_for(g->n, 256), 256>>>(rowptr, g->n, thr, d_cnt);
+        CU(cudaGetLastError());
+        CU(cudaMemcpy(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost));
+        if ((int64_t)cnt * per_hub <= budget) break;
+        thr *= 2;
+    }
+    g->n_hub = cnt;
+    g->hub_words = hw;
+    if (cnt > 0) {
+        int32_t* hub_vert = nullptr;
+        CU(cudaMalloc((void**)&g->hub_of, sizeof(int32_t) * (size_t)g->n));
+        CU(cudaMalloc((void**)&hub_vert, sizeof(int32_t) * (size_t)cnt));
+        CU(cudaMalloc((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw)));
+        CU(cudaMalloc((void**)&g->hub_pre, sizeof(uint32_t) * (size_t)(cnt * (hw / 8))));
+        CU(cudaMemset(d_cnt, 0, sizeof(int)));
+        CU(cudaMemset(g->hub_bits, 0, sizeof(unsigned long long) * (size_t)(cnt * hw)));
+        k_hub_list<Off><<<grid_for(g->n, 256), 256>>>(rowptr, g->n, thr, g->hub_of, hub_vert, d_cnt);
+        CU(cudaGetLastError());
+        k_hub_fill<Off><<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(rowptr, g->col, hub_vert, cnt, hw,
+                                                                               g->hub_bits);
+        CU(cudaGetLastError());
+        k_hub_pre<<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(g->hub_bits, cnt, hw, g->hub_pre);
+        CU(cudaGetLastError());
+        CU(cudaDeviceSynchronize());
+        cudaFree(hub_vert);
+    }
+    cudaFree(d_cnt);
+    return TRUSS_OK;
+}
+
 int truss_ensure_workspace(truss_graph* g) {
     if (g->ctr) return TRUSS_OK;
     const size_t m = (size_t)(g->m > 0 ? g->m : 1);
@@ -1752,13 +1906,15 @@ int truss_ensure_workspace(truss_graph* g) {
         g->ocap = (uint32_t)cap;
         for (int k = 0; k < 2; k++) CU(cudaMalloc((void**)&g->owner[k], sizeof(int2) * (size_t)cap));
     }
+    CU(cudaMalloc((void**)&g->lhub, sizeof(int32_t) * m));
     if (g->m > 0) {
+        TRY(g->off64 ? build_hubs<int64_t>(g) : build_hubs<int32_t>(g));
         if (g->off64)
             k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin,
-                                                           (int64_t*)g->rows);
+                                                           (int64_t*)g->rows, g->hub_of, g->lhub);
         else
             k_dmin<int32_t><<<grid_for(g->m, 256), 256>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin,
-                                                           (int32_t*)g->rows);
+                                                           (int32_t*)g->rows, g->hub_of, g->lhub);
         CU(cudaGetLastError());
         CU(cudaDeviceSynchronize());
     }
@@ -1770,6 +1926,14 @@ void truss_release_workspace(truss_graph* g) {
     cudaFree(g->dmin);
     cudaFree(g->rows);
     g->rows = nullptr;
+    cudaFree(g->lhub);
+    cudaFree(g->hub_of);
+    cudaFree(g->hub_bits);
+    cudaFree(g->hub_pre);
+    g->lhub = g->hub_of = nullptr;
+    g->hub_bits = nullptr;
+    g->hub_pre = nullptr;
+    g->n_hub = 0;
     for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) {
             cudaFree(g->fq[k][j]);
