@@ -269,6 +269,10 @@ TRUSS_API void truss_default_opts(truss_opts* opts);
  * never decreases along it; together with "every edge of trussness k lies in
  * >= k-2 triangles of edges of trussness >= k" this proves the result exact.
  *   stats   : may be NULL; filled only when opts->sync is set.
+ * Workspace: the first call on a graph allocates its peeling workspace and
+ * keeps it until truss_free (about 100 bytes per edge with int32 offsets,
+ * plus neighbour bitmaps of its highest-degree vertices within 128 bytes per
+ * edge and 32 GiB); TRUSS_ENOMEM when the device cannot hold it.
  */
 TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts* opts, truss_stats* stats, void* stream);
 
