@@ -270,7 +270,7 @@ TRUSS_API void truss_default_opts(truss_opts* opts);
  * >= k-2 triangles of edges of trussness >= k" this proves the result exact.
  *   stats   : may be NULL; filled only when opts->sync is set.
  * Workspace: the first call on a graph allocates its peeling workspace and
- * keeps it until truss_free (about 100 bytes per edge with int32 offsets,
+ * keeps it until truss_free (roughly 100 to 150 bytes per edge with int32 offsets,
  * plus neighbour bitmaps of its highest-degree vertices within 128 bytes per
  * edge and 32 GiB); TRUSS_ENOMEM when the device cannot hold it.
  */

@@ -63,8 +63,7 @@ struct truss_graph {
     void* rows = nullptr;   // per edge: shorter row bounds, longer row bounds (Off x 4)
     int32_t* lhub = nullptr;     // per edge: hub index of the longer row's vertex, -1 if none
     int32_t* hub_of = nullptr;   // per vertex: hub index, -1 if none
-    unsigned long long* hub_bits = nullptr;  // per hub: neighbour bitmap (hub_words words)
-    uint32_t* hub_pre = nullptr; // per hub: neighbours before each 512-bit block
+    unsigned long long* hub_bits = nullptr;  // per hub: hub_words words, blocks of {count before, 3 x 64 ids}
     int32_t n_hub = 0;
     int64_t hub_words = 0;
     int64_t max_updeg = 0;

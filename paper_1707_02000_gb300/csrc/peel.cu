@@ -130,9 +130,8 @@ struct Graph {
     const int32_t* __restrict__ dmin;  // min(d(u), d(v)) per edge
     const Off* __restrict__ rows;      // per edge: shorter row [a0, a1), longer row [b0, b1)
     const int32_t* __restrict__ lhub;  // per edge: hub index of the longer row's vertex, -1 if none
-    const unsigned long long* __restrict__ hbits;  // per hub: neighbour bitmap, hw words
-    const uint32_t* __restrict__ hpre;             // per hub: neighbours before each 512-bit block
-    int64_t hw;                                    // words per hub bitmap (a multiple of 8)
+    const unsigned long long* __restrict__ hbits;  // per hub: 32-byte blocks {count before, 3 x 64 ids}
+    int64_t hw;                                    // words per hub (4 per block)
     int2* ss;
     int64_t m;
     int hc;  // heavy chunk length (entries of the shorter row)
@@ -360,20 +359,21 @@ __device__ __forceinline__ void find2(const int32_t* __restrict__ a, Off lo, Off
 }
 
 // Slot of w in the row (starting at slot b0) of the vertex that owns hub h,
-// or -1: the bit of w in the hub's neighbour bitmap, and its rank = the
-// neighbours before w's 512-bit block (stored) + those in the block's words
-// before w's word + those below w in its word.  All loads are independent
-// (one round trip; the block's words share a 64-byte line).
+// or -1.  The hub's bitmap is cut into 32-byte blocks of 192 ids: word 0
+// holds the number of neighbours before the block, words 1-3 the bits.  One
+// probe reads one block (one sector): the bit of w, and its rank = the count
+// before the block + the bits of the block's earlier words + the bits below
+// w in its word.
 template <typename Off>
 __device__ __forceinline__ Off hub_find(const Graph<Off>& G, int32_t h, Off b0, int32_t w) {
-    const unsigned long long* B = G.hbits + (int64_t)h * G.hw;
-    const int64_t wi = w >> 6, wb = wi & ~(int64_t)7;
-    const unsigned long long word = __ldg(B + wi);
-    uint32_t rank = __ldg(G.hpre + (int64_t)h * (G.hw >> 3) + (w >> 9));
-#pragma unroll
-    for (int k = 0; k < 7; k++)
-        if (wb + k < wi) rank += (uint32_t)__popcll(__ldg(B + wb + k));
-    const int bit = w & 63;
+    const int32_t b = w / 192, r = w - b * 192;
+    const ulonglong2* B = reinterpret_cast<const ulonglong2*>(G.hbits + (int64_t)h * G.hw + 4 * (int64_t)b);
+    const ulonglong2 lo = __ldg(B), hi = __ldg(B + 1);
+    const int k = r >> 6, bit = r & 63;
+    const unsigned long long word = k == 0 ? lo.y : (k == 1 ? hi.x : hi.y);
+    uint32_t rank = (uint32_t)lo.x;
+    if (k > 0) rank += (uint32_t)__popcll(lo.y);
+    if (k > 1) rank += (uint32_t)__popcll(hi.x);
     rank += (uint32_t)__popcll(word & ((1ull << bit) - 1ull));
     return ((word >> bit) & 1ull) ? b0 + (Off)rank : (Off)-1;
 }
@@ -1143,10 +1143,10 @@ __global__ void k_dmin(const Off* __restrict__ rowptr, const int2* __restrict__ 
     }
 }
 
-// Hub bitmaps: for each vertex of degree >= the hub threshold, a bitmap
-// over vertex ids with its neighbours set and, per 512-bit block, the number
-// of neighbours before the block; ProcessSubLevel probes these rows through
-// hub_find instead of a binary search.
+// Hub bitmaps: for each vertex of degree >= the hub threshold, its
+// neighbours as bits over vertex ids in 32-byte blocks of 192 ids, each
+// block led by the number of neighbours before it; ProcessSubLevel probes
+// these rows through hub_find instead of a binary search.
 template <typename Off>
 __global__ void k_count_deg(const Off* __restrict__ rowptr, int32_t n, int64_t thr, int* cnt) {
     int c = 0;
@@ -1178,27 +1178,27 @@ __global__ void k_hub_fill(const Off* __restrict__ rowptr, const int32_t* __rest
         unsigned long long* B = bits + (int64_t)h * hw;
         for (Off j = rowptr[v] + threadIdx.x; j < rowptr[v + 1]; j += blockDim.x) {
             const int32_t w = col[j];
-            atomicOr(B + (w >> 6), 1ull << (w & 63));
+            const int32_t b = w / 192, r = w - b * 192;
+            atomicOr(B + 4 * (int64_t)b + 1 + (r >> 6), 1ull << (r & 63));
         }
     }
 }
 
-// per hub: exclusive prefix over its 512-bit blocks of the neighbour counts
-__global__ void k_hub_pre(const unsigned long long* __restrict__ bits, int32_t nhub, int64_t hw,
-                          uint32_t* __restrict__ pre) {
+// per hub: word 0 of each block <- neighbours in the blocks before it
+__global__ void k_hub_pre(unsigned long long* __restrict__ bits, int32_t nhub, int64_t hw) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
-    const int64_t nb = hw >> 3;
+    const int64_t nb = hw >> 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int32_t h = blockIdx.x; h < nhub; h += gridDim.x) {
-        const unsigned long long* B = bits + (int64_t)h * hw;
+        unsigned long long* B = bits + (int64_t)h * hw;
         if (threadIdx.x == 0) carry = 0;
         __syncthreads();
         for (int64_t base = 0; base < nb; base += blockDim.x) {
             const int64_t b = base + threadIdx.x;
             uint32_t c = 0;
             if (b < nb)
-                for (int k = 0; k < 8; k++) c += (uint32_t)__popcll(B[b * 8 + k]);
+                for (int k = 1; k < 4; k++) c += (uint32_t)__popcll(B[b * 4 + k]);
             uint32_t x = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -1209,7 +1209,7 @@ __global__ void k_hub_pre(const unsigned long long* __restrict__ bits, int32_t n
             __syncthreads();
             uint32_t before = carry;
             for (int w2 = 0; w2 < warp; w2++) before += wsum[w2];
-            if (b < nb) pre[(int64_t)h * nb + b] = before + x - c;
+            if (b < nb) B[b * 4] = before + x - c;
             __syncthreads();
             if (threadIdx.x == 0) {
                 uint32_t t = 0;
@@ -1233,7 +1233,7 @@ int process_blocks(const truss_graph* g) {
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
     return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, (const Off*)g->rows, g->lhub,
-                      g->hub_bits, g->hub_pre, g->hub_words, g->ss, g->m, g->hc, g->ocap};
+                      g->hub_bits, g->hub_words, g->ss, g->m, g->hc, g->ocap};
 }
 
 TuneTable tune_table_of(const truss_opts& o) {
@@ -1836,14 +1836,14 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 }  // namespace
 
 // Hub bitmaps for the vertices of degree >= thr, thr = 1024 doubled until
-// they fit a budget of 128 bytes per edge (at most 32 GiB): one bit per
-// vertex id plus 4 bytes per 512 ids for each hub.  On R-MAT scale 24 the
+// they fit a budget of 128 bytes per edge (at most 32 GiB): 32 bytes per 192
+// vertex ids for each hub.  On R-MAT scale 24 the
 // peel takes 3.65 s with the 32 GiB budget, 4.02 s with 8 GiB.
 template <typename Off>
 int build_hubs(truss_graph* g) {
     const Off* rowptr = (const Off*)g->rowptr;
-    const int64_t hw = (((int64_t)g->n + 511) / 512) * 8;
-    const int64_t per_hub = hw * 8 + (hw / 8) * 4;
+    const int64_t hw = (((int64_t)g->n + 191) / 192) * 4;
+    const int64_t per_hub = hw * 8;
     const int64_t budget = std::min<int64_t>((int64_t)32 << 30, 128 * g->m);
     int* d_cnt = nullptr;
     CU(cudaMalloc((void**)&d_cnt, sizeof(int)));
@@ -1864,7 +1864,6 @@ int build_hubs(truss_graph* g) {
         CU(cudaMalloc((void**)&g->hub_of, sizeof(int32_t) * (size_t)g->n));
         CU(cudaMalloc((void**)&hub_vert, sizeof(int32_t) * (size_t)cnt));
         CU(cudaMalloc((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw)));
-        CU(cudaMalloc((void**)&g->hub_pre, sizeof(uint32_t) * (size_t)(cnt * (hw / 8))));
         CU(cudaMemset(d_cnt, 0, sizeof(int)));
         CU(cudaMemset(g->hub_bits, 0, sizeof(unsigned long long) * (size_t)(cnt * hw)));
         k_hub_list<Off><<<grid_for(g->n, 256), 256>>>(rowptr, g->n, thr, g->hub_of, hub_vert, d_cnt);
@@ -1872,7 +1871,7 @@ int build_hubs(truss_graph* g) {
         k_hub_fill<Off><<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(rowptr, g->col, hub_vert, cnt, hw,
                                                                                g->hub_bits);
         CU(cudaGetLastError());
-        k_hub_pre<<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(g->hub_bits, cnt, hw, g->hub_pre);
+        k_hub_pre<<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(g->hub_bits, cnt, hw);
         CU(cudaGetLastError());
         CU(cudaDeviceSynchronize());
         cudaFree(hub_vert);
@@ -1930,10 +1929,8 @@ void truss_release_workspace(truss_graph* g) {
     cudaFree(g->lhub);
     cudaFree(g->hub_of);
     cudaFree(g->hub_bits);
-    cudaFree(g->hub_pre);
     g->lhub = g->hub_of = nullptr;
     g->hub_bits = nullptr;
-    g->hub_pre = nullptr;
     g->n_hub = 0;
     for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) {
