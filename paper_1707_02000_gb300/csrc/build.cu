@@ -183,8 +183,17 @@ __global__ void k_classify_vertices(const int64_t* __restrict__ rowptr, const in
         }
         warp_append(up > TRUSS_SUP_WARP_CAP && up <= TRUSS_SUP_BLOCK_CAP, (int32_t)u, big, nbig);
         warp_append(up > TRUSS_SUP_BLOCK_CAP, (int32_t)u, huge, nhuge);
-        if (d) atomicMax(&maxes[0], (unsigned long long)d);
-        if (up) atomicMax(&maxes[1], (unsigned long long)up);
+        // one atomic per warp for each maximum (same-address atomics from
+        // every vertex cost more than the rest of the kernel)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            d = max(d, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)d, o));
+            up = max(up, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)up, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (d) atomicMax(&maxes[0], (unsigned long long)d);
+            if (up) atomicMax(&maxes[1], (unsigned long long)up);
+        }
     }
 }
 
@@ -444,6 +453,22 @@ void truss_free_device(truss_graph* g) {
     truss_release_workspace(g);
 }
 
+// The library allocates from this process's default stream-ordered pool.
+// Its release threshold (default 0) returns freed memory to the driver at
+// every synchronisation, so each new graph would map its buffers again; keep
+// up to 16 GiB of freed pool memory for reuse instead.  The attribute belongs
+// to this process's pool and ends with it.
+static void keep_pool_memory(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = (uint64_t)16 << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[device] = true;
+}
+
 extern "C" int truss_build_csr(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t n, uint32_t flags,
                                void* stream, truss_graph** out) {
     if (!out) return TRUSS_EINVAL;
@@ -455,6 +480,7 @@ extern "C" int truss_build_csr(const int32_t* d_src, const int32_t* d_dst, int64
     if (!g) return TRUSS_ENOMEM;
     CU(cudaGetDevice(&g->device));
     CU(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+    keep_pool_memory(g->device);
     int rc = build_impl(d_src, d_dst, n_in, n, flags, s, g);
     if (rc != TRUSS_OK) {
         cudaStreamSynchronize(s);

@@ -85,5 +85,5 @@ struct truss_graph {
 // Implemented in support.cu: fills ss[e].x = S(e) for every internal edge.
 int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s);
 // Implemented in peel.cu.
-int truss_ensure_workspace(truss_graph* g);
+int truss_ensure_workspace(truss_graph* g, cudaStream_t s);
 void truss_release_workspace(truss_graph* g);

@@ -1666,7 +1666,7 @@ int check_opts(const truss_opts& o) {
 
 template <typename Off>
 int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_stats* st, cudaStream_t s) {
-    TRY(truss_ensure_workspace(g));
+    TRY(truss_ensure_workspace(g, s));
     const long long launches0 = truss_launch_count();
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     const bool timed = o.sync && st;
@@ -1787,7 +1787,7 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
 template <typename Off>
 int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr, int64_t ncurr,
                        int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant, cudaStream_t s) {
-    TRY(truss_ensure_workspace(g));
+    TRY(truss_ensure_workspace(g, s));
     const int64_t m = g->m;
     int32_t *inv = nullptr, *cur = nullptr;
     CU(cudaMallocAsync((void**)&cur, sizeof(int32_t) * (size_t)(ncurr > 0 ? ncurr : 1), s));
@@ -1840,20 +1840,21 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 // vertex ids for each hub.  On R-MAT scale 24 the
 // peel takes 3.65 s with the 32 GiB budget, 4.02 s with 8 GiB.
 template <typename Off>
-int build_hubs(truss_graph* g) {
+int build_hubs(truss_graph* g, cudaStream_t s) {
     const Off* rowptr = (const Off*)g->rowptr;
     const int64_t hw = (((int64_t)g->n + 191) / 192) * 4;
     const int64_t per_hub = hw * 8;
     const int64_t budget = std::min<int64_t>((int64_t)32 << 30, 128 * g->m);
     int* d_cnt = nullptr;
-    CU(cudaMalloc((void**)&d_cnt, sizeof(int)));
+    CU(cudaMallocAsync((void**)&d_cnt, sizeof(int), s));
     int64_t thr = 1024;
     int cnt = 0;
     for (;;) {
-        CU(cudaMemset(d_cnt, 0, sizeof(int)));
-        k_count_deg<Off><<<grid_for(g->n, 256), 256>>>(rowptr, g->n, thr, d_cnt);
+        CU(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
+        k_count_deg<Off><<<grid_for(g->n, 256), 256, 0, s>>>(rowptr, g->n, thr, d_cnt);
         CU(cudaGetLastError());
-        CU(cudaMemcpy(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpyAsync(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
         if ((int64_t)cnt * per_hub <= budget) break;
         thr *= 2;
     }
@@ -1861,26 +1862,27 @@ int build_hubs(truss_graph* g) {
     g->hub_words = hw;
     if (cnt > 0) {
         int32_t* hub_vert = nullptr;
-        CU(cudaMalloc((void**)&g->hub_of, sizeof(int32_t) * (size_t)g->n));
-        CU(cudaMalloc((void**)&hub_vert, sizeof(int32_t) * (size_t)cnt));
-        CU(cudaMalloc((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw)));
-        CU(cudaMemset(d_cnt, 0, sizeof(int)));
-        CU(cudaMemset(g->hub_bits, 0, sizeof(unsigned long long) * (size_t)(cnt * hw)));
-        k_hub_list<Off><<<grid_for(g->n, 256), 256>>>(rowptr, g->n, thr, g->hub_of, hub_vert, d_cnt);
+        CU(cudaMallocAsync((void**)&g->hub_of, sizeof(int32_t) * (size_t)g->n, s));
+        CU(cudaMallocAsync((void**)&hub_vert, sizeof(int32_t) * (size_t)cnt, s));
+        CU(cudaMallocAsync((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw), s));
+        CU(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
+        CU(cudaMemsetAsync(g->hub_bits, 0, sizeof(unsigned long long) * (size_t)(cnt * hw), s));
+        k_hub_list<Off><<<grid_for(g->n, 256), 256, 0, s>>>(rowptr, g->n, thr, g->hub_of, hub_vert, d_cnt);
         CU(cudaGetLastError());
-        k_hub_fill<Off><<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(rowptr, g->col, hub_vert, cnt, hw,
+        k_hub_fill<Off><<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256, 0, s>>>(rowptr, g->col, hub_vert, cnt, hw,
                                                                                g->hub_bits);
         CU(cudaGetLastError());
-        k_hub_pre<<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256>>>(g->hub_bits, cnt, hw);
+        k_hub_pre<<<std::min<int64_t>(cnt, (int64_t)g->sms * 8), 256, 0, s>>>(g->hub_bits, cnt, hw);
         CU(cudaGetLastError());
-        CU(cudaDeviceSynchronize());
-        cudaFree(hub_vert);
+        cudaFreeAsync(hub_vert, s);
     }
-    cudaFree(d_cnt);
+    cudaFreeAsync(d_cnt, s);
     return TRUSS_OK;
 }
 
-int truss_ensure_workspace(truss_graph* g) {
+// Allocations come from the stream-ordered pool and the setup kernels run on
+// stream s (one synchronisation at the end).
+int truss_ensure_workspace(truss_graph* g, cudaStream_t s) {
     if (g->ctr) return TRUSS_OK;
     const size_t m = (size_t)(g->m > 0 ? g->m : 1);
     // heavy chunk length: 64 entries (two per lane), longer when the graph is
@@ -1888,15 +1890,14 @@ int truss_ensure_workspace(truss_graph* g) {
     int64_t hc = 64;
     while ((int64_t)g->m + g->dmin_sum / hc >= ((int64_t)1 << 32) - 1) hc *= 2;
     g->hc = (int)hc;
-    CU(cudaMalloc((void**)&g->ss, sizeof(int2) * (m + 1)));
-    CU(cudaMalloc((void**)&g->dmin, sizeof(int32_t) * m));
-    CU(cudaMalloc(&g->rows, (g->off64 ? sizeof(int64_t) : sizeof(int32_t)) * 4 * m));
+    CU(cudaMallocAsync((void**)&g->ss, sizeof(int2) * (m + 1), s));
+    CU(cudaMallocAsync((void**)&g->dmin, sizeof(int32_t) * m, s));
+    CU(cudaMallocAsync(&g->rows, (g->off64 ? sizeof(int64_t) : sizeof(int32_t)) * 4 * m, s));
     for (int k = 0; k < 2; k++) {
-        for (int j = 0; j < 3; j++) CU(cudaMalloc((void**)&g->fq[k][j], sizeof(int32_t) * m));
-        CU(cudaMalloc((void**)&g->live[k], sizeof(int32_t) * m));
+        for (int j = 0; j < 3; j++) CU(cudaMallocAsync((void**)&g->fq[k][j], sizeof(int32_t) * m, s));
+        CU(cudaMallocAsync((void**)&g->live[k], sizeof(int32_t) * m, s));
     }
-    CU(cudaMalloc((void**)&g->ctr, sizeof(int) * C_TOTAL));
-    CU(cudaMalloc(&g->gctl, sizeof(GCtl)));
+    CU(cudaMallocAsync(&g->gctl, sizeof(GCtl), s));
     CU(cudaMallocHost((void**)&g->h_ctr, sizeof(int) * C_TOTAL));
     // chunk owner maps: enough for any sub-level of graphs up to moderate
     // size; larger chunk totals fall back to a search
@@ -1904,20 +1905,24 @@ int truss_ensure_workspace(truss_graph* g) {
         const int64_t want = (int64_t)g->m + g->dmin_sum / hc + 1;
         const int64_t cap = std::min<int64_t>(want, std::min<int64_t>(4 * (int64_t)g->m + 1024, (int64_t)UINT32_MAX));
         g->ocap = (uint32_t)cap;
-        for (int k = 0; k < 2; k++) CU(cudaMalloc((void**)&g->owner[k], sizeof(int2) * (size_t)cap));
+        for (int k = 0; k < 2; k++) CU(cudaMallocAsync((void**)&g->owner[k], sizeof(int2) * (size_t)cap, s));
     }
-    CU(cudaMalloc((void**)&g->lhub, sizeof(int32_t) * m));
+    CU(cudaMallocAsync((void**)&g->lhub, sizeof(int32_t) * m, s));
     if (g->m > 0) {
-        TRY(g->off64 ? build_hubs<int64_t>(g) : build_hubs<int32_t>(g));
+        TRY(g->off64 ? build_hubs<int64_t>(g, s) : build_hubs<int32_t>(g, s));
         if (g->off64)
-            k_dmin<int64_t><<<grid_for(g->m, 256), 256>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin,
-                                                           (int64_t*)g->rows, g->hub_of, g->lhub);
+            k_dmin<int64_t><<<grid_for(g->m, 256), 256, 0, s>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin,
+                                                                 (int64_t*)g->rows, g->hub_of, g->lhub);
         else
-            k_dmin<int32_t><<<grid_for(g->m, 256), 256>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin,
-                                                           (int32_t*)g->rows, g->hub_of, g->lhub);
+            k_dmin<int32_t><<<grid_for(g->m, 256), 256, 0, s>>>((const int32_t*)g->rowptr, g->el, g->m, g->dmin,
+                                                                 (int32_t*)g->rows, g->hub_of, g->lhub);
         CU(cudaGetLastError());
-        CU(cudaDeviceSynchronize());
     }
+    // the counter block last: a workspace with ctr set is complete
+    int* ctr = nullptr;
+    CU(cudaMallocAsync((void**)&ctr, sizeof(int) * C_TOTAL, s));
+    CU(cudaStreamSynchronize(s));
+    g->ctr = ctr;
     return TRUSS_OK;
 }
 
@@ -2008,7 +2013,7 @@ extern "C" void truss_default_opts(truss_opts* o) {
 extern "C" int truss_support(truss_graph* g, int32_t* d_support, void* stream) {
     if (!g || (g->m > 0 && !d_support)) return TRUSS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    TRY(truss_ensure_workspace(g));
+    TRY(truss_ensure_workspace(g, s));
     TRY(truss_support_internal(g, g->ss, s));
     if (g->m > 0) k_truss_out<<<grid_for(g->m, 256), 256, 0, s>>>(g->ss, g->m, g->perm, d_support, 0);
     CU(cudaGetLastError());
