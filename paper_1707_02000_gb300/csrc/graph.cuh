@@ -27,14 +27,21 @@
 //   live[2] int32[m]  edges each Scan found above its level: the only edges
 //                     the next Scan visits (a list that shrinks level by level)
 //   owner[2] int2     chunk -> {edge, chunk index in its row}, each side
+//   rows   Off[4m]    per edge: shorter row [a0, a1), longer row [b0, b1)
+//   lhub   int32[m]   per edge: hub index of the longer row's vertex, -1
+//   hub_of int32[n]   per vertex: hub index, -1 (degree below the threshold)
+//   hub_bits          per hub: 32-byte blocks of 192 vertex ids, {count of
+//                     neighbours before the block, 3 x 64 neighbour bits}
 //   ctr    int[...]   device counters (see peel.cu)
 #pragma once
 #include "common.cuh"
 
 #define TRUSS_STAMP_NONE 0x7fffffff
 
-// Support-kernel split: vertices whose upper degree d+(u) exceeds this are
-// handled by the block-per-vertex kernel instead of warp-per-vertex.
+// Support-kernel classes by upper degree d+(u): the warp-per-vertex kernel
+// takes d+(u) <= TRUSS_SUP_WARP_CAP (its 128-entry instance when no d+(u)
+// exceeds TRUSS_SUP_SPLIT), the block-per-vertex kernel up to
+// TRUSS_SUP_BLOCK_CAP, a global-memory kernel beyond.
 #define TRUSS_SUP_SPLIT 128
 #define TRUSS_SUP_WARP_CAP 256
 #define TRUSS_SUP_BLOCK_CAP 12288
