@@ -35,8 +35,10 @@ namespace {
 constexpr int SW_WARPS = 8;  // warps per block, warp-per-vertex kernel
 constexpr int SW_SPLIT = TRUSS_SUP_SPLIT;  // rows up to here go to the smaller instance
 
-// S(e) lives in ss[e].x; the int view puts it at index 2e.
-__device__ __forceinline__ void add_support(int* S2, int32_t e, int v) { atomicAdd(S2 + 2 * (int64_t)e, v); }
+// S accumulates in a plain int32[m] array (half the footprint of the
+// {S, stamp} pairs, so more of the random per-triangle atomics hit L2); the
+// pairs are written from it once at the end.
+__device__ __forceinline__ void add_support(int* S, int32_t e, int v) { atomicAdd(S + e, v); }
 
 // Largest index p in [0, d) with P[p] <= idx (P ascending, P[0] = 0).
 __device__ __forceinline__ int seg_of(const int* P, int d, int idx) {
@@ -61,7 +63,7 @@ __device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, in
 template <typename Off, int CAP>
 __global__ void __launch_bounds__(SW_WARPS * 32)
     k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
-                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S2) {
+                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S) {
     __shared__ int sK[SW_WARPS][CAP];
     __shared__ int sC[SW_WARPS][CAP];
     __shared__ int sP[SW_WARPS][CAP + 1];
@@ -116,17 +118,17 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
             if (r1 < d && K[r1] == w1) {
                 atomicAdd(&C[r1], 1);  // edge {u, w}
                 atomicAdd(&C[p1], 1);  // edge {u, v}
-                add_support(S2, x1, 1);  // edge {v, w}
+                add_support(S, x1, 1);  // edge {v, w}
             }
             if (two && r2 < d && K[r2] == w2) {
                 atomicAdd(&C[r2], 1);
                 atomicAdd(&C[p2], 1);
-                add_support(S2, x2, 1);
+                add_support(S, x2, 1);
             }
         }
         __syncwarp();
         for (int p = lane; p < d; p += 32)
-            if (C[p]) add_support(S2, __ldg(eid + up0 + p), C[p]);
+            if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
         __syncwarp();
     }
 }
@@ -163,7 +165,7 @@ template <typename Off>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
-                    int* __restrict__ S2) {
+                    int* __restrict__ S) {
     extern __shared__ int smem[];
     int* K = smem;
     int* C = smem + cap;
@@ -210,17 +212,17 @@ __global__ void __launch_bounds__(SB_THREADS)
             if (r1 < d && K[r1] == w1) {
                 atomicAdd(&C[r1], 1);
                 atomicAdd(&C[p1], 1);
-                add_support(S2, x1, 1);
+                add_support(S, x1, 1);
             }
             if (two && r2 < d && K[r2] == w2) {
                 atomicAdd(&C[r2], 1);
                 atomicAdd(&C[p2], 1);
-                add_support(S2, x2, 1);
+                add_support(S, x2, 1);
             }
         }
         __syncthreads();
         for (int p = threadIdx.x; p < d; p += SB_THREADS)
-            if (C[p]) add_support(S2, __ldg(eid + up0 + p), C[p]);
+            if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
         __syncthreads();
     }
 }
@@ -231,7 +233,7 @@ template <typename Off>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_global(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                      const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts,
-                     int* __restrict__ S2) {
+                     int* __restrict__ S) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
         const int32_t u = verts[i];
@@ -245,39 +247,39 @@ __global__ void __launch_bounds__(SB_THREADS)
                 Off r = find_dev<Off>(col, pv + 1, up1, w);
                 if (r >= 0) {
                     cuv++;
-                    add_support(S2, __ldg(eid + r), 1);
-                    add_support(S2, __ldg(eid + q), 1);
+                    add_support(S, __ldg(eid + r), 1);
+                    add_support(S, __ldg(eid + q), 1);
                 }
             }
             cuv = warp_sum(cuv);
-            if (lane == 0 && cuv) add_support(S2, __ldg(eid + pv), cuv);
+            if (lane == 0 && cuv) add_support(S, __ldg(eid + pv), cuv);
         }
     }
 }
 
-__global__ void k_init_ss(int2* __restrict__ ss, int64_t m) {
+__global__ void k_pack_ss(const int* __restrict__ S, int2* __restrict__ ss, int64_t m) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        ss[e] = make_int2(0, TRUSS_STAMP_NONE);
+        ss[e] = make_int2(S[e], TRUSS_STAMP_NONE);
 }
 
 template <typename Off>
 int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     const Off* rowptr = (const Off*)g->rowptr;
     const Off* eo = (const Off*)g->eo;
-    int* S2 = (int*)ss;
-    k_init_ss<<<grid_for(g->m, 256), 256, 0, s>>>(ss, g->m);
-    CU(cudaGetLastError());
-    truss_note_launch();
+    // accumulator: the first light-frontier buffer (int32[m], idle until the
+    // peel starts)
+    int* S = g->fq[0][0];
+    CU(cudaMemsetAsync(S, 0, sizeof(int) * (size_t)(g->m > 0 ? g->m : 1), s));
     if (g->n > 0 && g->m > 0) {
         // one warp-per-vertex instance: the 128-entry one when no N+(u) is
         // longer (8 blocks an SM), else the 256-entry one (6 blocks an SM);
         // two instances run one after the other cost more than either
         int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
         if (g->max_updeg <= SW_SPLIT)
-            k_support_warp<Off, SW_SPLIT><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
+            k_support_warp<Off, SW_SPLIT><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S);
         else
             k_support_warp<Off, TRUSS_SUP_WARP_CAP>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S2);
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S);
         CU(cudaGetLastError());
         truss_note_launch();
     }
@@ -290,13 +292,18 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
             attr_set[sizeof(Off) == 8] = true;
         }
         int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
-        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S2);
+        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S);
         CU(cudaGetLastError());
         truss_note_launch();
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
-        k_support_global<Off><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S2);
+        k_support_global<Off><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S);
+        CU(cudaGetLastError());
+        truss_note_launch();
+    }
+    if (g->m > 0) {
+        k_pack_ss<<<grid_for(g->m, 256), 256, 0, s>>>(S, ss, g->m);
         CU(cudaGetLastError());
         truss_note_launch();
     }
