@@ -141,25 +141,32 @@ def algorithmic_bytes(st, n):
     return sup, peel
 
 
-def kernel_source_hash():
+# translation unit that defines each reported kernel
+KERNEL_SOURCE = {"k_persistent": "peel.cu", "k_process": "peel.cu", "k_gprocess": "peel.cu",
+                 "k_support_warp": "support.cu"}
+
+
+def kernel_source_hash(kernel: str = "k_persistent"):
+    """Hash of the sources a kernel is compiled from: its .cu file and every
+    shared header."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1707_02000_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    files = [KERNEL_SOURCE.get(kernel, "peel.cu")] + sorted(f for f in os.listdir(d) if f.endswith(".cuh"))
+    for f in files:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
     ent = rec.get(workload, {}).get(kernel)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    if not ent or ent.get("source_hash") != kernel_source_hash(kernel):
         return None
     return ent.get("bytes_per_launch")
 
