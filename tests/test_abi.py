@@ -72,3 +72,50 @@ def test_no_oracle_in_product_path():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "truss_oracle" not in txt, f
+
+
+def _header_defines():
+    out = {}
+    txt = open(HEADER).read()
+    for name, val in re.findall(r"^#define TRUSS_(\w+)\s+\(?(-?\d+)u?\)?", txt, flags=re.M):
+        out[name] = int(val)
+    out["NOALLOC_MAX_VERTICES"] = 1 << 22 if "(1 << 22)" in txt else None
+    return out
+
+
+def _struct_fields(tag):
+    txt = open(HEADER).read()
+    body = re.search(r"typedef struct " + tag + r"\s*\{(.*?)\}\s*" + tag + ";", txt, flags=re.S)
+    assert body, tag
+    fields = []
+    for line in re.sub(r"/\*.*?\*/", "", body.group(1), flags=re.S).split(";"):
+        m = re.search(r"(\w+)\s*(\[\s*\d+\s*\])?\s*$", line.strip())
+        if m:
+            fields.append(m.group(1))
+    return fields
+
+
+def test_binding_constants_match_the_header(pkt):
+    """Every constant the binding mirrors has the header's value."""
+    d = _header_defines()
+    pairs = {"OK": pkt.OK, "EINVAL": pkt.EINVAL, "ENOMEM": pkt.ENOMEM, "ECUDA": pkt.ECUDA,
+             "ETIMEOUT": pkt.ETIMEOUT, "EOVERFLOW": pkt.EOVERFLOW, "EBADGRAPH": pkt.EBADGRAPH,
+             "EDEVICE": pkt.EDEVICE, "ENOTSUP": pkt.ENOTSUP, "ETOOBIG": pkt.ETOOBIG,
+             "DEGREE_ORDER": pkt.DEGREE_ORDER, "OFFSETS64": pkt.OFFSETS64,
+             "LOOP_PLAIN": pkt.LOOP_PLAIN, "LOOP_PERSISTENT": pkt.LOOP_PERSISTENT,
+             "LOOP_PERSISTENT_LAT": pkt.LOOP_PERSISTENT_LAT, "LOOP_PERSISTENT_OCC": pkt.LOOP_PERSISTENT_OCC,
+             "LOOP_GRAPH": pkt.LOOP_GRAPH, "VAR_AUTO": pkt.VAR_AUTO, "VAR_THREAD": pkt.VAR_THREAD,
+             "VAR_GROUP": pkt.VAR_GROUP, "VAR_WARP": pkt.VAR_WARP, "VAR_LEARNED": pkt.VAR_LEARNED,
+             "SCHED_FEATURES": pkt.SCHED_FEATURES, "SCHED_VARIANTS": pkt.SCHED_VARIANTS,
+             "SCHED_PARAMS": pkt.SCHED_PARAMS, "TUNE_CLASSES": pkt.TUNE_CLASSES,
+             "NOALLOC_MAX_VERTICES": pkt.NOALLOC_MAX_VERTICES}
+    wrong = {k: (d.get(k), v) for k, v in pairs.items() if d.get(k) != v}
+    assert not wrong, wrong
+
+
+def test_binding_structs_follow_the_header_field_order(pkt):
+    """The ctypes structures list the header's fields in the header's order
+    (a reordered field would shift every later one)."""
+    assert [f for f, _ in pkt.Opts._fields_] == _struct_fields("truss_opts")
+    assert [f for f, _ in pkt.Stats._fields_] == _struct_fields("truss_stats")
+    assert list(pkt.TRACE_DTYPE.names) == _struct_fields("truss_sublevel_trace")
