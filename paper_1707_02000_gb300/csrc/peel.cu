@@ -1,20 +1,25 @@
 // Level-synchronous peeling (Algorithms 4 and 5, §III) on the device.
 //
-// Scan (K2): one coalesced pass over the {S, stamp} words, 16 bytes (two
-// edges) per thread per step; edges with S = l join curr (warp ballot + one
-// atomic per warp), and the minimum support above l is reduced on the side
-// so that an empty level can jump straight to the next live one.
+// Scan (K2): the first Scan reads all {S, stamp} words (16 bytes, two edges,
+// per load); every Scan writes the edges above its level to a live list that
+// the next Scan reads instead of all m edges.  Edges with S = l join curr,
+// split into light and heavy lists; a block step places its appends with one
+// block prefix sum and at most three atomics.  The minimum support above l
+// is reduced on the side, so an empty level jumps straight to the next live
+// one.
 //
 // ProcessSubLevel (K3): for every e1 = {u, v} in curr, the common neighbours
-// w of u and v are found by binary search of each entry of the shorter row in
-// the longer one.  Each triangle {e1, e2, e3} whose other two edges are
-// unprocessed lowers e2 (resp. e3) by one when its support is above l and e3
-// (resp. e2) is not in curr or has a larger id than e1: the two-sided reading
-// of Algorithm 5, which prints only the e2 case.  The decrement is atomicSub;
-// an edge whose old value was l+1 joins next; a thread that pushed an edge
-// below l adds the 1 back (the clamp-and-restore of Algorithm 5), so the
-// final value is max(l, S - #triangles removed).  The rule is symmetric in e2
-// and e3, so which of them is {u,w} or {v,w} does not matter.
+// w of u and v are found by searching each entry of the shorter row in the
+// longer one: through registers when the longer row is short, through the
+// neighbour bitmap when its vertex is a hub, else by binary search (two keys
+// per lane in lockstep).  Each triangle {e1, e2, e3} whose other two edges
+// are unprocessed lowers e2 (resp. e3) by one when its support is above l
+// and e3 (resp. e2) is not in curr or has a larger id than e1: the two-sided
+// reading of Algorithm 5, which prints only the e2 case.  The decrement is
+// atomicSub; an edge whose old value was l+1 joins next; a thread that
+// pushed an edge below l adds the 1 back (the clamp-and-restore of Algorithm
+// 5), so the final value is max(l, S - #triangles removed).  The rule is
+// symmetric in e2 and e3, so which of them is {u,w} or {v,w} does not matter.
 //
 // Work mapping.  A frontier is kept as two lists:
 //   light  edges whose shorter row has <= LIGHT entries; each is walked by a
@@ -24,14 +29,18 @@
 //   heavy  longer rows, cut into chunks of hc entries.  Appending a heavy
 //          edge reserves its chunk range with one 64-bit atomic on
 //          (edge count << 32 | chunk total), so the chunk bases are monotone
-//          in list order and any warp can map chunk index -> edge by binary
-//          search.  All warps of the grid share all chunks, so the few huge
-//          rows of a small late frontier spread over the whole GPU.
+//          in list order; the owner map records each chunk's edge and place
+//          in the row (beyond its capacity a warp finds the edge by binary
+//          search over the chunk bases).  All warps of the grid share all
+//          chunks, so the few huge rows of a small late frontier spread over
+//          the whole GPU.
 //
 // Loop forms: PLAIN launches Scan / ProcessSubLevel from the host and reads
 // the frontier size back after every phase (the direct transcription of
 // Algorithm 4's loop); PERSISTENT runs the whole loop in one cooperative
-// kernel whose phases are separated by a grid barrier with a time limit.
+// kernel whose phases are separated by a grid barrier with a time limit (in
+// two register budgets); GRAPH runs it as one CUDA graph whose control
+// kernel picks each next phase on the device.
 #include <algorithm>
 #include <climits>
 #include <cstring>
