@@ -231,12 +231,12 @@ struct Appender {
                 atomicAdd(cnt.dsum, sm->dsum);
                 atomicMax(cnt.dmax, sm->dmax);
             }
-            sm->lbase = kl ? atomicAdd(cnt.nl, kl) : 0;
-            if (kh) {
-                const unsigned long long old = atomicAdd(cnt.hc, ((unsigned long long)kh << 32) | run);
-                sm->hq0 = (int)(old >> 32);
-                sm->hb0 = (uint32_t)old;
-            }
+            // both reservations in flight before either result is used
+            const int lb = kl ? atomicAdd(cnt.nl, kl) : 0;
+            const unsigned long long old = kh ? atomicAdd(cnt.hc, ((unsigned long long)kh << 32) | run) : 0ull;
+            sm->lbase = lb;
+            sm->hq0 = (int)(old >> 32);
+            sm->hb0 = (uint32_t)old;
         }
         __syncthreads();
         for (int i = t; i < kl; i += PT) out.light[sm->lbase + i] = sm->lbuf[i];
@@ -786,13 +786,14 @@ __device__ void scan_level(int2* ss, const int32_t* in, int64_t nin, int32_t* ke
                 runc += tc;
             }
             const int tl = (int)(run & 0xffff), th = (int)((run >> 16) & 0xffff), tv = (int)(run >> 32);
-            sm->lbase = tl ? atomicAdd(cnt.nl, tl) : 0;
-            if (th) {
-                const unsigned long long old = atomicAdd(cnt.hc, ((unsigned long long)th << 32) | runc);
-                sm->hq0 = (int)(old >> 32);
-                sm->hb0 = (uint32_t)old;
-            }
-            sm->bbase = tv ? atomicAdd(cnt.nlive, tv) : 0;
+            // the three reservations in flight before any result is used
+            const int lb = tl ? atomicAdd(cnt.nl, tl) : 0;
+            const unsigned long long old = th ? atomicAdd(cnt.hc, ((unsigned long long)th << 32) | runc) : 0ull;
+            const int vb = tv ? atomicAdd(cnt.nlive, tv) : 0;
+            sm->lbase = lb;
+            sm->hq0 = (int)(old >> 32);
+            sm->hb0 = (uint32_t)old;
+            sm->bbase = vb;
         }
         __syncthreads();
         const unsigned long long ex = sm->wtot[warp] + x -
