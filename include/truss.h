@@ -67,6 +67,14 @@ typedef struct truss_graph truss_graph;
 #define TRUSS_OFFSETS64 2u    /* store row offsets as int64 (else int32,
                                  switched to int64 automatically when 2m
                                  exceeds INT32_MAX)                          */
+#define TRUSS_CORE_ORDER 4u   /* relabel vertices in a degeneracy order (§IV-B:
+                                 vertices ordered by k-core): the order in
+                                 which a level-synchronous k-core peel on the
+                                 device removes them, ties by label, so each
+                                 vertex has at most its coreness of
+                                 neighbours after it.  Costs one host round
+                                 trip per peel round at build time.  Takes
+                                 precedence over TRUSS_DEGREE_ORDER.         */
 
 /*
  * truss_build_csr -- build the device graph of §III / Fig. 2 from a raw edge

@@ -27,6 +27,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBADGRAPH, EDEVICE, ENOTSUP, ETOOBIG
 NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
+CORE_ORDER = 4
 LOOP_PLAIN, LOOP_PERSISTENT, LOOP_PERSISTENT_LAT, LOOP_PERSISTENT_OCC, LOOP_GRAPH = 0, 1, 2, 3, 4
 VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP, VAR_LEARNED = -1, 0, 1, 2, 3
 SCHED_FEATURES, SCHED_VARIANTS, SCHED_PARAMS, TUNE_CLASSES = 5, 3, 1357, 128
@@ -285,10 +286,14 @@ class Graph:
         _check(_lib.truss_sync(self._h, _stream(stream)), "truss_sync")
 
 
-def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = False, stream=None) -> Graph:
-    """Device graph from CUDA int32 tensors ``src``, ``dst`` (raw pairs)."""
+def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = False, core_order: bool = False,
+              stream=None) -> Graph:
+    """Device graph from CUDA int32 tensors ``src``, ``dst`` (raw pairs);
+    ``core_order`` relabels in a degeneracy (k-core) order instead of by
+    degree."""
     assert src.dtype == dst.dtype and str(src.dtype) == "torch.int32" and src.numel() == dst.numel()
-    flags = (DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
+    flags = ((DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
+             | (CORE_ORDER if core_order else 0))
     h = ctypes.c_void_p()
     k = src.numel()
     _check(_lib.truss_build_csr(_dptr(src) if k else None, _dptr(dst) if k else None, k, n, flags,

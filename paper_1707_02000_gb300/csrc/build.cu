@@ -134,6 +134,69 @@ __global__ void k_degree_keys(const int64_t* __restrict__ rowptr, int32_t n, int
         keys[v] = (uint64_t)(rowptr[v + 1] - rowptr[v]) << nb | (uint64_t)v;
 }
 
+// ---- degeneracy order (TRUSS_CORE_ORDER): level-synchronous k-core peel.
+// Level k: a scan removes every live vertex of degree <= k (round t); then,
+// round after round, the vertices removed in the last round lower the degree
+// of their live neighbours, and a neighbour whose degree falls from k + 1 to
+// k is removed in the next round.  step[v] = round of v's removal (-1 while
+// live); the order is by (step, label).
+__global__ void k_core_init(const int64_t* __restrict__ rowptr, int32_t n, int32_t* __restrict__ deg,
+                            int32_t* __restrict__ step) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        deg[v] = (int32_t)(rowptr[v + 1] - rowptr[v]);
+        step[v] = -1;
+    }
+}
+
+// live vertices of degree <= k join round t; the smallest live degree above
+// k is reduced into *minv (for an empty scan's jump)
+__global__ void k_core_scan(int32_t n, const int32_t* __restrict__ deg, int32_t* __restrict__ step, int32_t k,
+                            int32_t t, int32_t* __restrict__ out, int* cnt, int* minv) {
+    int mn = INT_MAX;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        bool take = false;
+        if (v < n && step[v] < 0) {
+            const int d = deg[v];
+            if (d <= k) {
+                step[v] = t;
+                take = true;
+            } else {
+                mn = min(mn, d);
+            }
+        }
+        warp_append(take, (int32_t)v, out, cnt);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
+    if ((threadIdx.x & 31) == 0 && mn != INT_MAX) atomicMin(minv, mn);
+}
+
+// a warp per vertex removed in round t: its live neighbours lose one degree;
+// one that falls to k is removed in round t + 1
+__global__ void k_core_round(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ cur, int32_t ncur, int32_t* __restrict__ deg,
+                             int32_t* __restrict__ step, int32_t k, int32_t t, int32_t* __restrict__ next,
+                             int* nnext) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ncur; i += nwarps) {
+        const int32_t v = cur[i];
+        for (int64_t j = rowptr[v] + lane; j < rowptr[v + 1]; j += 32) {
+            const int32_t u = col[j];
+            if (step[u] < 0 && atomicSub(deg + u, 1) == k + 1) {
+                step[u] = t + 1;
+                next[atomicAdd(nnext, 1)] = u;
+            }
+        }
+    }
+}
+
+__global__ void k_core_keys(const int32_t* __restrict__ step, int32_t n, int nb, uint64_t* __restrict__ keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = (uint64_t)step[v] << nb | (uint64_t)v;
+}
+
 __global__ void k_order(const uint64_t* __restrict__ keys, int32_t n, uint64_t mask, int32_t* __restrict__ order,
                         int32_t* __restrict__ newid) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -230,6 +293,64 @@ void free_csr(Csr64& c, cudaStream_t s) {
     c = Csr64();
 }
 
+// Removal rounds of the k-core peel (see k_core_round) as sort keys
+// (round << nb | v); *rounds receives the number of rounds.
+static int core_steps(const Csr64& c, int32_t n, int nb, uint64_t* keys, int32_t* rounds, cudaStream_t s) {
+    const int B = 256;
+    int32_t *deg = nullptr, *step = nullptr, *fa = nullptr, *fb = nullptr;
+    int* ctr = nullptr;
+    CU(talloc(&deg, n, s));
+    CU(talloc(&step, n, s));
+    CU(talloc(&fa, n, s));
+    CU(talloc(&fb, n, s));
+    CU(talloc(&ctr, 2, s));
+    k_core_init<<<grid_for(n, B), B, 0, s>>>(c.rowptr, n, deg, step);
+    CU(cudaGetLastError());
+    int h[2];
+    int64_t removed = 0;
+    int32_t k = 0, t = 0;
+    const int rblocks = grid_for((int64_t)n * 32, B, (int64_t)152 * 16);
+    while (removed < n) {
+        const int init[2] = {0, INT_MAX};
+        CU(cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        k_core_scan<<<grid_for(n, B), B, 0, s>>>(n, deg, step, k, t, fa, ctr, ctr + 1);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h[0] == 0) {
+            if (h[1] == INT_MAX) break;  // nothing live (cannot happen while removed < n)
+            k = h[1];
+            continue;
+        }
+        removed += h[0];
+        int32_t* cur = fa;
+        int32_t* nxt = fb;
+        int32_t ncur = h[0];
+        for (;;) {
+            CU(cudaMemsetAsync(ctr, 0, sizeof(int), s));
+            k_core_round<<<rblocks, B, 0, s>>>(c.rowptr, c.col, cur, ncur, deg, step, k, t, nxt, ctr);
+            CU(cudaGetLastError());
+            CU(cudaMemcpyAsync(h, ctr, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            t++;
+            if (h[0] == 0) break;
+            removed += h[0];
+            ncur = h[0];
+            std::swap(cur, nxt);
+        }
+        k++;
+    }
+    k_core_keys<<<grid_for(n, B), B, 0, s>>>(step, n, nb, keys);
+    CU(cudaGetLastError());
+    *rounds = t;
+    tfree(deg, s);
+    tfree(step, s);
+    tfree(fa, s);
+    tfree(fb, s);
+    tfree(ctr, s);
+    return TRUSS_OK;
+}
+
 // CSR (64-bit offsets) from 2m sorted unique directed keys.
 int csr_from_keys(const uint64_t* U, int64_t len, int32_t n, int nb, Csr64& c, cudaStream_t s) {
     const int B = 256;
@@ -301,16 +422,26 @@ int build_impl(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t
     TRY(csr_from_keys(U, two_m, n, nb, c0, s));
     Csr64 c1;
     uint64_t* U1 = U;
-    const bool relabel = (flags & TRUSS_DEGREE_ORDER) && n > 1;
+    const bool core_order = (flags & TRUSS_CORE_ORDER) && n > 1;
+    const bool relabel = ((flags & TRUSS_DEGREE_ORDER) || core_order) && n > 1;
     int32_t* newid = nullptr;
     if (relabel) {
         // 4: rank by (degree, label); a degree is below 2^nb
         uint64_t *dk = nullptr, *dtmp = nullptr, *dsorted = nullptr;
         CU(talloc(&dk, n, s));
         CU(talloc(&dtmp, n, s));
-        k_degree_keys<<<grid_for(n, B), B, 0, s>>>(c0.rowptr, n, nb, dk);
+        int key_bits = 2 * nb;
+        if (core_order) {
+            int32_t rounds = 0;
+            TRY(core_steps(c0, n, nb, dk, &rounds, s));
+            int rb = 1;
+            while (rb < 31 && (1ll << rb) <= (int64_t)rounds) rb++;
+            key_bits = nb + rb;
+        } else {
+            k_degree_keys<<<grid_for(n, B), B, 0, s>>>(c0.rowptr, n, nb, dk);
+        }
         CU(cudaGetLastError());
-        CU(prims::radix_sort_u64(dk, dtmp, n, 2 * nb, &dsorted, s));
+        CU(prims::radix_sort_u64(dk, dtmp, n, key_bits, &dsorted, s));
         CU(cudaMallocAsync((void**)&g->order, sizeof(int32_t) * (size_t)n, s));
         CU(talloc(&newid, n, s));
         k_order<<<grid_for(n, B), B, 0, s>>>(dsorted, n, mask, g->order, newid);

@@ -101,7 +101,7 @@ def test_binding_constants_match_the_header(pkt):
     pairs = {"OK": pkt.OK, "EINVAL": pkt.EINVAL, "ENOMEM": pkt.ENOMEM, "ECUDA": pkt.ECUDA,
              "ETIMEOUT": pkt.ETIMEOUT, "EOVERFLOW": pkt.EOVERFLOW, "EBADGRAPH": pkt.EBADGRAPH,
              "EDEVICE": pkt.EDEVICE, "ENOTSUP": pkt.ENOTSUP, "ETOOBIG": pkt.ETOOBIG,
-             "DEGREE_ORDER": pkt.DEGREE_ORDER, "OFFSETS64": pkt.OFFSETS64,
+             "DEGREE_ORDER": pkt.DEGREE_ORDER, "OFFSETS64": pkt.OFFSETS64, "CORE_ORDER": pkt.CORE_ORDER,
              "LOOP_PLAIN": pkt.LOOP_PLAIN, "LOOP_PERSISTENT": pkt.LOOP_PERSISTENT,
              "LOOP_PERSISTENT_LAT": pkt.LOOP_PERSISTENT_LAT, "LOOP_PERSISTENT_OCC": pkt.LOOP_PERSISTENT_OCC,
              "LOOP_GRAPH": pkt.LOOP_GRAPH, "VAR_AUTO": pkt.VAR_AUTO, "VAR_THREAD": pkt.VAR_THREAD,

@@ -345,6 +345,26 @@ def _scan_sequence(m, tau, step):
     return seq, visited
 
 
+@pytest.mark.parametrize("loop", ["plain", "persistent_lat", "graph"])
+def test_core_order_is_a_degeneracy_order_and_exact(pkt, loop):
+    """With TRUSS_CORE_ORDER the internal labels follow the device k-core
+    peel: every vertex has at most its coreness (brute-force minimum-degree
+    removal) of neighbours with a higher label; trussness is unchanged."""
+    from brute import coreness
+
+    graphs = [gg.workload("rmat10_ef8"), gg.chung_lu(6000, 2.1, 12.0, 600.0, seed=21),
+              gg.rgg2d(5000, 14.0, seed=22), gg.small_random(40, 0.3, seed=23)]
+    for g in graphs:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, core_order=True)
+        eu, ev, want = oracle.truss_of_edges(g.n, g.src, g.dst)
+        assert np.array_equal(host(G.decompose(loop=_loop(pkt, loop))), want), g.name
+        rp, col, eid, eo, order = (host(x) for x in G.csr())
+        core = coreness(g.n, eu, ev)
+        up = rp[1:] - eo  # neighbours after each internal vertex
+        assert np.all(up <= core[order]), g.name
+        G.free()
+
+
 def _want_bps(st):
     per_level = st["dmin_sum"] // (st["max_support"] + 1)
     return 6 if per_level >= 1 << 24 or st["dmin_sum"] >= 1 << 34 else 4
