@@ -62,6 +62,8 @@ def bind(path: str):
     lib.or_certify.restype = I64
     lib.or_certify_sample.argtypes = [I32, I64, i32p, i32p, i32p, i32p, i64p, I64, i64p]
     lib.or_certify_sample.restype = I64
+    lib.or_ktruss_components.argtypes = [I32, I64, i32p, i32p, i32p, I32, i32p]
+    lib.or_ktruss_components.restype = I64
     return lib
 
 
@@ -232,3 +234,17 @@ def certify_sample(n: int, eu, ev, tau, step, sample):
                               sample.shape[0], ctypes.byref(fb))
     _check(r, "certify_sample")
     return int(r), int(fb.value)
+
+
+def ktruss_components(n: int, eu, ev, tau, k: int):
+    """The k-trusses as components (§II): per edge, the smallest vertex label
+    of its component among the edges of trussness >= k, or -1; and the
+    number of components."""
+    lib = _load()
+    eu, pu = _i32(eu)
+    ev, pv = _i32(ev)
+    tau, pt = _i32(tau)
+    comp = np.empty(max(eu.size, 1), np.int32)
+    nc = lib.or_ktruss_components(n, eu.size, pu, pv, pt, k, comp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    _check(nc, "ktruss_components")
+    return comp[: eu.size].copy(), int(nc)

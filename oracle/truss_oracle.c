@@ -615,3 +615,49 @@ int64_t or_certify_sample(int32_t n, int64_t m, const int32_t* eu, const int32_t
     free(adj); free(cur); free(mark); free(off);
     return bad;
 }
+
+/* ---- k-trusses as subgraphs (§II: a k-truss is a maximal connected
+ * subgraph whose every edge lies in >= k-2 of its triangles).  The k-trusses
+ * of a graph are the connected components of the edges of trussness >= k;
+ * comp[e] = the smallest vertex label of e's component, -1 when tau[e] < k.
+ * Plain union-find over those edges (union by smaller label, path halving).
+ * Returns the number of components. */
+static int32_t uf_root(int32_t* p, int32_t x) {
+    while (p[x] != x) {
+        p[x] = p[p[x]];
+        x = p[x];
+    }
+    return x;
+}
+
+int64_t or_ktruss_components(int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, const int32_t* tau,
+                             int32_t k, int32_t* comp) {
+    if (n < 0 || m < 0) return -1;
+    int32_t* p = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!p) return -2;
+    for (int32_t v = 0; v < n; v++) p[v] = v;
+    for (int64_t e = 0; e < m; e++) {
+        if (tau[e] < k) continue;
+        const int32_t a = uf_root(p, eu[e]), b = uf_root(p, ev[e]);
+        if (a < b) p[b] = a;
+        else if (b < a) p[a] = b;
+    }
+    /* the root of a tree is its smallest label: a root is only ever hooked
+     * under a smaller one */
+    int64_t ncomp = 0;
+    for (int64_t e = 0; e < m; e++) {
+        if (tau[e] < k) {
+            comp[e] = -1;
+            continue;
+        }
+        comp[e] = uf_root(p, eu[e]);
+    }
+    for (int32_t v = 0; v < n; v++) p[v] = (p[v] == v) ? -1 : 0; /* reuse: mark roots */
+    for (int64_t e = 0; e < m; e++)
+        if (comp[e] >= 0 && p[comp[e]] == -1) {
+            p[comp[e]] = 1;
+            ncomp++;
+        }
+    free(p);
+    return ncomp;
+}

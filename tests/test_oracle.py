@@ -362,3 +362,67 @@ def test_sampled_certificate():
     s2 = step.copy()
     s2[np.argmax(tau)] = 0
     assert oracle.certify_sample(g.n, eu, ev, tau, s2, sample[:10])[0] > 0
+
+
+# ---------------------------------------------------------- k-truss listing
+
+def _components_by_scipy(n, eu, ev, tau, k):
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as cg
+
+    sel = tau >= k
+    A = sp.coo_matrix((np.ones(int(sel.sum())), (eu[sel], ev[sel])), shape=(n, n))
+    _, lab = cg.connected_components(A, directed=False)
+    # label a component by its smallest vertex (vertices on selected edges)
+    first = {}
+    for v in np.unique(np.concatenate([eu[sel], ev[sel]])).tolist():
+        first.setdefault(int(lab[v]), v)
+    comp = np.full(eu.size, -1, np.int32)
+    comp[sel] = [first[int(lab[u])] for u in eu[sel].tolist()]
+    return comp, len(first)
+
+
+def test_ktruss_components_match_connected_components():
+    """The oracle's k-truss components equal scipy's connected components of
+    the edges of trussness >= k, for every k of several graphs."""
+    graphs = [gg.workload("rmat10_ef8"), gg.chung_lu(3000, 2.1, 14.0, 300.0, seed=31),
+              gg.small_random(30, 0.25, seed=32), gg.rgg2d(2000, 10.0, seed=33)]
+    for g in graphs:
+        eu, ev, tau = oracle.truss_of_edges(g.n, g.src, g.dst)
+        for k in range(2, int(tau.max()) + 2):
+            got, nc = oracle.ktruss_components(g.n, eu, ev, tau, k)
+            want, wnc = _components_by_scipy(g.n, eu, ev, tau, k)
+            assert np.array_equal(got, want), (g.name, k)
+            assert nc == wnc, (g.name, k)
+
+
+def test_ktruss_components_closed_forms():
+    """A disjoint K4 (vertices 0-3), K5 (10-14) and a path: the 3-trusses are
+    the two cliques, the 4-trusses too, the only 5-truss is K5."""
+    import itertools
+
+    pairs = list(itertools.combinations(range(4), 2)) + list(itertools.combinations(range(10, 15), 2))
+    pairs += [(20, 21), (21, 22), (3, 20)]
+    n = 23
+    src = np.array([a for a, _ in pairs], np.int32)
+    dst = np.array([b for _, b in pairs], np.int32)
+    eu, ev, tau = oracle.truss_of_edges(n, src, dst)
+    in_k4 = (eu < 4) & (ev < 4)
+    in_k5 = (eu >= 10) & (ev < 15)
+    for k, labels, ncomp in ((3, {0, 10}, 2), (4, {0, 10}, 2), (5, {10}, 1), (6, set(), 0)):
+        comp, nc = oracle.ktruss_components(n, eu, ev, tau, k)
+        assert nc == ncomp and set(comp[comp >= 0].tolist()) == labels, k
+        assert np.all(comp[in_k4] == (0 if k <= 4 else -1))
+        assert np.all(comp[in_k5] == (10 if k <= 5 else -1))
+        assert np.all(comp[~in_k4 & ~in_k5] == -1)
+    comp, nc = oracle.ktruss_components(n, eu, ev, tau, 2)  # k = 2: the graph's components
+    assert nc == 2 and set(comp.tolist()) == {0, 10}
+
+
+def test_fig1_two_3_trusses_by_the_oracle():
+    n, rows = _read_rows("fig1_standin.txt")
+    uv = np.array([[int(x) for x in r.split()] for r in rows])
+    eu, ev = oracle.canonical(n, uv[:, 0].astype(np.int32), uv[:, 1].astype(np.int32))
+    tau = oracle.truss(n, eu, ev)
+    _, nc = oracle.ktruss_components(n, eu, ev, tau, 3)
+    assert nc == 2

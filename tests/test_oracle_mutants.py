@@ -32,6 +32,10 @@ MUTANTS = {
     "sublevel_next_on_wrong_value": ("if (S[e2] == l) next[nnext++] = e2;",
                                      "if (S[e2] == l + 1) next[nnext++] = e2;"),
     "sublevel_swapped_edge_roles": ("int32_t e2 = (a == v) ? f_aw : f_bw;", "int32_t e2 = (a == u) ? f_aw : f_bw;"),
+    "components_hook_smaller_under_larger": ("if (a < b) p[b] = a;\n        else if (b < a) p[a] = b;",
+                                             "if (a < b) p[a] = b;\n        else if (b < a) p[b] = a;"),
+    "components_keep_low_trussness_edges": ("        if (tau[e] < k) continue;\n        const int32_t a",
+                                            "        const int32_t a"),
 }
 
 
@@ -45,6 +49,8 @@ def _battery():
     yield T.test_random_graphs_up_to_14_vertices
     yield T.test_sublevel_frontiers_are_order_free
     yield T.test_all_graphs_on_six_vertices
+    yield T.test_ktruss_components_closed_forms
+    yield T.test_ktruss_components_match_connected_components
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
