@@ -256,6 +256,25 @@ typedef struct truss_stats {
     int32_t reserved;
 } truss_stats;
 
+/*
+ * truss_ktruss_components -- the k-trusses of the graph as subgraphs (§II:
+ * a k-truss is a maximal connected subgraph whose every edge lies in at
+ * least k-2 of its triangles): the connected components of the edges whose
+ * trussness is >= k.
+ *   d_truss : device int32[m], canonical order (as truss_decompose writes it).
+ *   k       : any value; k <= 2 takes every edge.
+ *   d_comp  : device int32[m], canonical order (written): the smallest input
+ *             vertex label of the edge's k-truss, or -1 when the edge's
+ *             trussness is below k.
+ *   h_ncomp : host int64 (may be NULL): the number of k-trusses; when given
+ *             the call waits for the result.
+ * Errors: TRUSS_EINVAL for null arguments; TRUSS_EDEVICE if a union-find
+ * loop hit its step bound (only on a corrupted state; reported when h_ncomp
+ * is given).  Allocates and frees 8 bytes per vertex in the call.
+ */
+TRUSS_API int truss_ktruss_components(truss_graph* g, const int32_t* d_truss, int32_t k, int32_t* d_comp,
+                                      int64_t* h_ncomp, void* stream);
+
 /* Fill *opts with defaults: persistent loop, heuristic variants, no sync,
  * level jumps on, 10 s wait limit, no sub-level recording. */
 TRUSS_API void truss_default_opts(truss_opts* opts);

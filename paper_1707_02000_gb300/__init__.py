@@ -39,7 +39,7 @@ EXPORTS = (
     "truss_edge_list", "truss_csr_copy", "truss_support", "truss_default_opts", "truss_decompose",
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
     "truss_decompose_batch", "truss_sched_features", "truss_sched_init", "truss_sched_grad",
-    "truss_sched_train", "truss_sched_predict", "truss_autotune",
+    "truss_sched_train", "truss_sched_predict", "truss_autotune", "truss_ktruss_components",
 )
 
 
@@ -89,6 +89,7 @@ def _declare(lib):
     lib.truss_edge_list.argtypes = [vp, vp, vp, vp]
     lib.truss_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.truss_support.argtypes = [vp, vp, vp]
+    lib.truss_ktruss_components.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.truss_default_opts.argtypes = [ctypes.POINTER(Opts)]
     lib.truss_default_opts.restype = None
     lib.truss_decompose.argtypes = [vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
@@ -274,6 +275,17 @@ class Graph:
                                         _dptr(nxt) if self.m else None, ctypes.byref(k), variant,
                                         _stream(stream)), "truss_peel_sublevel")
         return nxt[: k.value]
+
+    def ktruss_components(self, tau, k: int, stream=None):
+        """The k-trusses: per edge (canonical order, CUDA int32 tensor) the
+        smallest input vertex label of its component among the edges of
+        trussness >= k, or -1; and the number of components."""
+        comp = self._empty(self.m)
+        nc = ctypes.c_int64()
+        _check(_lib.truss_ktruss_components(self._h, _dptr(tau) if self.m else None, k,
+                                            _dptr(comp) if self.m else None, ctypes.byref(nc), _stream(stream)),
+               "truss_ktruss_components")
+        return comp, int(nc.value)
 
     def autotune(self, repeats: int = 1, stream=None):
         """Autotuned variant table (int8[TUNE_CLASSES]) for this graph."""

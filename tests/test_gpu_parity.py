@@ -473,3 +473,47 @@ def test_batch_rejects_ids_outside_their_graph(pkt):
     with pytest.raises(pkt.TrussError) as ex:
         pkt.decompose_batch([a, b])
     assert ex.value.status == pkt.EBADGRAPH
+
+
+# ---------------------------------------------------------- k-truss listing
+
+@pytest.mark.parametrize("order", ["degree", "core", "input"])
+def test_ktruss_components_match_oracle(pkt, order):
+    """Every k-truss (component of the edges of trussness >= k, labelled by
+    its smallest input vertex) equals the oracle's, for every k, in every
+    internal vertex order."""
+    import itertools
+
+    pairs = list(itertools.combinations(range(4), 2)) + list(itertools.combinations(range(10, 15), 2))
+    pairs += [(20, 21), (21, 22), (3, 20)]
+    cliques = gg.EdgeList(23, np.array([a for a, _ in pairs], np.int32), np.array([b for _, b in pairs], np.int32),
+                          "cliques")
+    graphs = [cliques, gg.workload("rmat10_ef8"), gg.chung_lu(6000, 2.1, 12.0, 600.0, seed=41),
+              gg.rgg2d(5000, 14.0, seed=42), gg.small_random(40, 0.3, seed=43)]
+    for g in graphs:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, degree_order=order == "degree", core_order=order == "core")
+        eu, ev, want_tau = oracle.truss_of_edges(g.n, g.src, g.dst)
+        tau = G.decompose()
+        assert np.array_equal(host(tau), want_tau)
+        for k in sorted({2, 3, int(want_tau.max()), int(want_tau.max()) + 1} | set(range(2, 8))):
+            comp, nc = G.ktruss_components(tau, k)
+            want, wnc = oracle.ktruss_components(g.n, eu, ev, want_tau, k)
+            assert np.array_equal(host(comp), want), (g.name, k)
+            assert nc == wnc, (g.name, k)
+        G.free()
+
+
+def test_ktruss_components_full_size(pkt):
+    """The bench workload: the k-trusses for k = 3, 20 and the top level,
+    from the device trussness, equal the oracle's components of the same
+    trussness."""
+    g = gg.workload("chunglu_n2^20_d20")
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    tau = G.decompose()
+    th = host(tau)
+    eu, ev = oracle.canonical(g.n, g.src, g.dst)
+    for k in (3, 20, int(th.max())):
+        comp, nc = G.ktruss_components(tau, k)
+        want, wnc = oracle.ktruss_components(g.n, eu, ev, th, k)
+        assert np.array_equal(host(comp), want) and nc == wnc, k
+    G.free()
