@@ -257,6 +257,15 @@ typedef struct truss_stats {
 } truss_stats;
 
 /*
+ * truss_triangle_count -- the number of triangles T of the graph (§II; the
+ * sum of all supports is 3T): the support kernels' walk (Algorithm 3, each
+ * triangle found once at its lowest vertex) without edge ids or per-edge
+ * atomics.  *h_count (host) receives T.  Synchronous on the stream.
+ * Errors: TRUSS_EINVAL for null arguments.
+ */
+TRUSS_API int truss_triangle_count(truss_graph* g, int64_t* h_count, void* stream);
+
+/*
  * truss_ktruss_components -- the k-trusses of the graph as subgraphs (§II:
  * a k-truss is a maximal connected subgraph whose every edge lies in at
  * least k-2 of its triangles): the connected components of the edges whose

@@ -40,6 +40,7 @@ EXPORTS = (
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
     "truss_decompose_batch", "truss_sched_features", "truss_sched_init", "truss_sched_grad",
     "truss_sched_train", "truss_sched_predict", "truss_autotune", "truss_ktruss_components",
+    "truss_triangle_count",
 )
 
 
@@ -90,6 +91,7 @@ def _declare(lib):
     lib.truss_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.truss_support.argtypes = [vp, vp, vp]
     lib.truss_ktruss_components.argtypes = [vp, vp, i32, vp, vp, vp]
+    lib.truss_triangle_count.argtypes = [vp, vp, vp]
     lib.truss_default_opts.argtypes = [ctypes.POINTER(Opts)]
     lib.truss_default_opts.restype = None
     lib.truss_decompose.argtypes = [vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
@@ -275,6 +277,12 @@ class Graph:
                                         _dptr(nxt) if self.m else None, ctypes.byref(k), variant,
                                         _stream(stream)), "truss_peel_sublevel")
         return nxt[: k.value]
+
+    def triangle_count(self, stream=None) -> int:
+        """Number of triangles (each counted once)."""
+        t = ctypes.c_int64()
+        _check(_lib.truss_triangle_count(self._h, ctypes.byref(t), _stream(stream)), "truss_triangle_count")
+        return int(t.value)
 
     def ktruss_components(self, tau, k: int, stream=None):
         """The k-trusses: per edge (canonical order, CUDA int32 tensor) the

@@ -59,11 +59,14 @@ __device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, in
     return lo;
 }
 
-// Vertices u with d+(u) <= CAP (longer rows go to the block kernels).
-template <typename Off, int CAP>
+// Vertices u with d+(u) <= CAP (longer rows go to the block kernels).  With
+// COUNT the kernels only count triangles into *tri (no edge ids, no
+// per-edge atomics).
+template <typename Off, int CAP, bool COUNT = false>
 __global__ void __launch_bounds__(SW_WARPS * 32)
     k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
-                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S) {
+                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S,
+                   unsigned long long* __restrict__ tri = nullptr) {
     __shared__ int sK[SW_WARPS][CAP];
     __shared__ int sC[SW_WARPS][CAP];
     __shared__ int sP[SW_WARPS][CAP + 1];
@@ -73,6 +76,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
     int* C = sC[warp];
     int* P = sP[warp];
     Off* E = sE[warp];
+    unsigned long long ntri = 0;
     const int64_t nwarps = (int64_t)gridDim.x * SW_WARPS;
     for (int64_t u = blockIdx.x * (int64_t)SW_WARPS + warp; u < n; u += nwarps) {
         const Off up0 = eo[u], up1 = rowptr[u + 1];
@@ -111,25 +115,35 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
             const int p2 = two ? seg_of(P, d, i2) : p1;
             const Off q1 = E[p1] + (idx - P[p1]);  // N+(v) starts at E[p] (staged)
             const Off q2 = two ? E[p2] + (i2 - P[p2]) : q1;
-            const int w1 = __ldg(col + q1), x1 = __ldg(eid + q1);
-            const int w2 = __ldg(col + q2), x2 = __ldg(eid + q2);
+            const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
+            const int w2 = __ldg(col + q2), x2 = COUNT ? 0 : __ldg(eid + q2);
             const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
             const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
-            if (r1 < d && K[r1] == w1) {
-                atomicAdd(&C[r1], 1);  // edge {u, w}
-                atomicAdd(&C[p1], 1);  // edge {u, v}
-                add_support(S, x1, 1);  // edge {v, w}
-            }
-            if (two && r2 < d && K[r2] == w2) {
-                atomicAdd(&C[r2], 1);
-                atomicAdd(&C[p2], 1);
-                add_support(S, x2, 1);
+            const bool t1 = r1 < d && K[r1] == w1, t2 = two && r2 < d && K[r2] == w2;
+            if constexpr (COUNT) {
+                ntri += (unsigned)t1 + (unsigned)t2;
+            } else {
+                if (t1) {
+                    atomicAdd(&C[r1], 1);  // edge {u, w}
+                    atomicAdd(&C[p1], 1);  // edge {u, v}
+                    add_support(S, x1, 1);  // edge {v, w}
+                }
+                if (t2) {
+                    atomicAdd(&C[r2], 1);
+                    atomicAdd(&C[p2], 1);
+                    add_support(S, x2, 1);
+                }
             }
         }
         __syncwarp();
-        for (int p = lane; p < d; p += 32)
-            if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
+        if constexpr (!COUNT)
+            for (int p = lane; p < d; p += 32)
+                if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
         __syncwarp();
+    }
+    if constexpr (COUNT) {
+        ntri = warp_sum(ntri);
+        if (lane == 0 && ntri) atomicAdd(tri, ntri);
     }
 }
 
@@ -161,12 +175,13 @@ __device__ int block_scan_incl(int x, int* wsum) {
 }
 
 // One block per listed vertex; cap entries of K, C, P in dynamic shared memory.
-template <typename Off>
+template <typename Off, bool COUNT = false>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
-                    int* __restrict__ S) {
+                    int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr) {
     extern __shared__ int smem[];
+    unsigned long long ntri = 0;
     int* K = smem;
     int* C = smem + cap;
     int* P = smem + 2 * cap;  // cap + 1 entries
@@ -205,35 +220,46 @@ __global__ void __launch_bounds__(SB_THREADS)
             const int p2 = two ? seg_of(P, d, i2) : p1;
             const Off q1 = __ldg(eo + K[p1]) + (idx - P[p1]);
             const Off q2 = two ? __ldg(eo + K[p2]) + (i2 - P[p2]) : q1;
-            const int w1 = __ldg(col + q1), x1 = __ldg(eid + q1);
-            const int w2 = __ldg(col + q2), x2 = __ldg(eid + q2);
+            const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
+            const int w2 = __ldg(col + q2), x2 = COUNT ? 0 : __ldg(eid + q2);
             const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
             const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
-            if (r1 < d && K[r1] == w1) {
-                atomicAdd(&C[r1], 1);
-                atomicAdd(&C[p1], 1);
-                add_support(S, x1, 1);
-            }
-            if (two && r2 < d && K[r2] == w2) {
-                atomicAdd(&C[r2], 1);
-                atomicAdd(&C[p2], 1);
-                add_support(S, x2, 1);
+            const bool t1 = r1 < d && K[r1] == w1, t2 = two && r2 < d && K[r2] == w2;
+            if constexpr (COUNT) {
+                ntri += (unsigned)t1 + (unsigned)t2;
+            } else {
+                if (t1) {
+                    atomicAdd(&C[r1], 1);
+                    atomicAdd(&C[p1], 1);
+                    add_support(S, x1, 1);
+                }
+                if (t2) {
+                    atomicAdd(&C[r2], 1);
+                    atomicAdd(&C[p2], 1);
+                    add_support(S, x2, 1);
+                }
             }
         }
         __syncthreads();
-        for (int p = threadIdx.x; p < d; p += SB_THREADS)
-            if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
+        if constexpr (!COUNT)
+            for (int p = threadIdx.x; p < d; p += SB_THREADS)
+                if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
         __syncthreads();
+    }
+    if constexpr (COUNT) {
+        ntri = warp_sum(ntri);
+        if ((threadIdx.x & 31) == 0 && ntri) atomicAdd(tri, ntri);
     }
 }
 
 // Vertices whose N+(u) exceeds shared memory: one block per vertex, one warp
 // per v in N+(u), probes by binary search in the global row of u.
-template <typename Off>
+template <typename Off, bool COUNT = false>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_global(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                      const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts,
-                     int* __restrict__ S) {
+                     int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr) {
+    unsigned long long ntri = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
         const int32_t u = verts[i];
@@ -247,13 +273,23 @@ __global__ void __launch_bounds__(SB_THREADS)
                 Off r = find_dev<Off>(col, pv + 1, up1, w);
                 if (r >= 0) {
                     cuv++;
-                    add_support(S, __ldg(eid + r), 1);
-                    add_support(S, __ldg(eid + q), 1);
+                    if constexpr (!COUNT) {
+                        add_support(S, __ldg(eid + r), 1);
+                        add_support(S, __ldg(eid + q), 1);
+                    }
                 }
             }
-            cuv = warp_sum(cuv);
-            if (lane == 0 && cuv) add_support(S, __ldg(eid + pv), cuv);
+            if constexpr (COUNT) {
+                ntri += (unsigned)cuv;
+            } else {
+                cuv = warp_sum(cuv);
+                if (lane == 0 && cuv) add_support(S, __ldg(eid + pv), cuv);
+            }
         }
+    }
+    if constexpr (COUNT) {
+        ntri = warp_sum(ntri);
+        if (lane == 0 && ntri) atomicAdd(tri, ntri);
     }
 }
 
@@ -310,7 +346,66 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     return TRUSS_OK;
 }
 
+// Triangle count: the support kernels' walk without edge ids or per-edge
+// atomics (each triangle u < v < w counted once at u).
+template <typename Off>
+int count_impl(truss_graph* g, unsigned long long* d_tri, cudaStream_t s) {
+    const Off* rowptr = (const Off*)g->rowptr;
+    const Off* eo = (const Off*)g->eo;
+    CU(cudaMemsetAsync(d_tri, 0, sizeof(unsigned long long), s));
+    if (g->n > 0 && g->m > 0) {
+        int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
+        if (g->max_updeg <= SW_SPLIT)
+            k_support_warp<Off, SW_SPLIT, true>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, nullptr, d_tri);
+        else
+            k_support_warp<Off, TRUSS_SUP_WARP_CAP, true>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, nullptr, d_tri);
+        CU(cudaGetLastError());
+        truss_note_launch();
+    }
+    if (g->n_sup_big > 0) {
+        const int cap = TRUSS_SUP_BLOCK_CAP;
+        const size_t smem = sizeof(int) * (size_t)(3 * cap + 1);
+        static bool attr_set[2] = {false, false};
+        if (!attr_set[sizeof(Off) == 8]) {
+            CU(cudaFuncSetAttribute(k_support_block<Off, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+            attr_set[sizeof(Off) == 8] = true;
+        }
+        int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
+        k_support_block<Off, true><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big,
+                                                                   g->n_sup_big, cap, nullptr, d_tri);
+        CU(cudaGetLastError());
+        truss_note_launch();
+    }
+    if (g->n_sup_huge > 0) {
+        int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
+        k_support_global<Off, true><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge,
+                                                                  g->n_sup_huge, nullptr, d_tri);
+        CU(cudaGetLastError());
+        truss_note_launch();
+    }
+    return TRUSS_OK;
+}
+
 }  // namespace
+
+extern "C" int truss_triangle_count(truss_graph* g, int64_t* h_count, void* stream) {
+    if (!g || !h_count) return TRUSS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* d_tri = nullptr;
+    CU(cudaMallocAsync((void**)&d_tri, sizeof(unsigned long long), s));
+    int rc = g->off64 ? count_impl<int64_t>(g, d_tri, s) : count_impl<int32_t>(g, d_tri, s);
+    unsigned long long h = 0;
+    if (rc == TRUSS_OK) {
+        CU(cudaMemcpyAsync(&h, d_tri, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        *h_count = (int64_t)h;
+    }
+    cudaFreeAsync(d_tri, s);
+    return rc;
+}
 
 int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s) {
     return g->off64 ? support_impl<int64_t>(g, ss, s) : support_impl<int32_t>(g, ss, s);

@@ -517,3 +517,22 @@ def test_ktruss_components_full_size(pkt):
         want, wnc = oracle.ktruss_components(g.n, eu, ev, th, k)
         assert np.array_equal(host(comp), want) and nc == wnc, k
     G.free()
+
+
+def test_triangle_count(pkt):
+    """The triangle-count mode of the support kernels gives T = (sum of the
+    oracle's supports) / 3, with int32 and int64 row offsets, and the
+    decomposition's own count on the bench workload."""
+    for g in (gg.workload("rmat10_ef8"), gg.chung_lu(6000, 2.1, 12.0, 600.0, seed=51), gg.rgg2d(5000, 14.0, seed=52),
+              gg.small_random(40, 0.3, seed=53)):
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        T = int(oracle.support(g.n, eu, ev).astype(np.int64).sum()) // 3
+        for off64 in (False, True):
+            G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, offsets64=off64)
+            assert G.triangle_count() == T, (g.name, off64)
+            G.free()
+    g = gg.workload("chunglu_n2^20_d20")
+    G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+    _, st = G.decompose(stats=True)
+    assert G.triangle_count() == st["triangles"]
+    G.free()
