@@ -119,3 +119,31 @@ def test_binding_structs_follow_the_header_field_order(pkt):
     assert [f for f, _ in pkt.Opts._fields_] == _struct_fields("truss_opts")
     assert [f for f, _ in pkt.Stats._fields_] == _struct_fields("truss_stats")
     assert list(pkt.TRACE_DTYPE.names) == _struct_fields("truss_sublevel_trace")
+
+
+def test_header_is_plain_c_and_links(pkt, tmp_path):
+    """A C99 program (no C++, no CUDA headers) includes truss.h, links
+    libtruss.so and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(
+        '#include "truss.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        "    truss_opts o;\n"
+        "    truss_default_opts(&o);\n"
+        '    printf("%d %d %d %s\\n", o.loop, (int)sizeof(truss_opts), (int)sizeof(truss_stats),\n'
+        "           truss_strerror(TRUSS_EINVAL));\n"
+        "    return truss_build_csr(NULL, NULL, 0, 0, 0, NULL, NULL) == TRUSS_EINVAL ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(pkt.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                           os.path.join(ROOT, "include"), str(src), "-L", libdir, "-ltruss",
+                           "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.split()[:3] == [str(pkt.LOOP_PERSISTENT), "80", "96"]
