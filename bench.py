@@ -11,11 +11,12 @@ with the CSR already in HBM.  The reported form is the persistent loop with
 the learned sub-level scheduler, whose cost model is trained before timing
 (outside the timed region) on two other graphs of the same family (seeds 101
 and 102); the host-driven loop and the persistent loop with the fixed
-heuristic are timed beside it.  Every step is timed with CUDA events on the
-stream the library launches on; L2 is flushed (a 256 MiB write) between
-steps, outside the timed events.  Under torchrun each rank runs its own
-replica on its own GPU (the decomposition does not shard) and
-the line reports the sum of edges over the slowest rank's time.
+heuristic, and the graph-driven loop, are timed beside it.  Every step is
+timed with CUDA events on the stream the library launches on; L2 is flushed
+(a 256 MiB write) between steps, outside the timed events.  Under torchrun
+each rank runs its own replica on its own GPU (the peel exchanges state
+every sub-level, so one decomposition does not shard) and the line reports
+the sum of edges over the slowest rank's time.
 """
 from __future__ import annotations
 
