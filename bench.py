@@ -5,18 +5,26 @@ device-resident graph, one JSON line on stdout.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 A step is one whole decomposition: support (Algorithm 3) and the level loop
-(Algorithms 4-5) over the Chung-Lu power-law workload (2^20 vertices,
-exponent 2.1, mean degree 20, expected degrees clipped at 2^14, seed 2),
-with the CSR already in HBM.  The reported form is the persistent loop with
-the learned sub-level scheduler, whose cost model is trained before timing
-(outside the timed region) on two other graphs of the same family (seeds 101
-and 102); the host-driven loop and the persistent loop with the fixed
-heuristic, and the graph-driven loop, are timed beside it.  Every step is
+(Algorithms 4-5) over the R-MAT scale-24 workload (edge factor 16,
+a/b/c/d = .57/.19/.19/.05, seed 4, int64 row offsets; m = 260,381,693), with
+the CSR in HBM.  The reported form is the persistent loop with the learned
+sub-level scheduler, whose cost model is trained before timing (outside the
+timed region) on other graphs of the workload families.  Every step is
 timed with CUDA events on the stream the library launches on; L2 is flushed
-(a 256 MiB write) between steps, outside the timed events.  Under torchrun
-each rank runs its own replica on its own GPU (the peel exchanges state
-every sub-level, so one decomposition does not shard) and the line reports
-the sum of edges over the slowest rank's time.
+(a 256 MiB write) between steps, outside the timed events.  The per-graph
+workspace of the peel (row records, hub bitmaps, min-degree table) is built
+by the first decomposition of a graph, which is a warm-up step, so the timed
+steps exclude it, as they exclude the CSR build (preprocessing, like the
+paper's vertex ordering); the end-to-end leg includes both.
+
+The line's ``configs`` block times the five workloads of the method's
+evaluation under each level-loop form (host-driven plain loop, persistent
+loop with the fixed heuristic, persistent loop with the learned scheduler,
+graph-driven loop) and gives each phase's algorithmic bytes over its device
+time against the measured HBM peak.  Under torchrun each rank runs its own
+replica on its own GPU (the peel exchanges state every sub-level, so one
+decomposition does not shard) and the line reports the sum of edges over
+the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -35,13 +43,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edges/s of full truss decomposition + % HBM peak; persistent+learned vs plain"
 UNIT = "edges/s"
-WORKLOAD = "chunglu_n2^20_d20"
-WORKLOAD_DESC = ("Chung-Lu power-law graph, 2^20 vertices, degree exponent 2.1, mean degree 20, "
-                 "max expected degree 2^14, seed 2, int32 CSR + int32 Eid/support")
-# bounded CPU sample of the same generator family for the oracle timings
-CPU_SAMPLE = dict(n=1 << 17, gamma=2.1, mean_deg=20.0, max_deg=float(1 << 14), seed=2)
-CPU_SAMPLE_DESC = ("oracle (serial Algorithm 1 peel, 1 core) on a Chung-Lu sample of the same family: "
-                   "2^17 vertices, exponent 2.1, mean degree 20, max expected degree 2^14, seed 2")
+WORKLOAD = "rmat24_ef16"
+WORKLOAD_DESC = {
+    "rmat10_ef8": "R-MAT scale 10, edge factor 8, a/b/c/d=.57/.19/.19/.05, seed 1, int32 CSR",
+    "chunglu_n2^20_d20": ("Chung-Lu power-law graph, 2^20 vertices, degree exponent 2.1, mean degree 20, "
+                          "max expected degree 2^14, seed 2, int32 CSR + int32 Eid/support"),
+    "rgg2d_n2^21_d32": "2-D random geometric graph, 2^21 vertices on the unit square, mean degree 32, seed 3, int32 CSR",
+    "rmat24_ef16": ("R-MAT scale 24, edge factor 16 (2^28 samples), a/b/c/d=.57/.19/.19/.05, seed 4, "
+                    "int32 ids, int64 row offsets"),
+    "chunglu_batch4096": ("4096 Chung-Lu graphs in one decomposition, graph i seed 1000+i, vertices log-uniform "
+                          "in [64, 8192], mean degree log-uniform in [8, 64], exponent 2.3"),
+}
+# the five workloads in the order of the method's evaluation configs
+CONFIG_WORKLOADS = ("rmat10_ef8", "chunglu_n2^20_d20", "rgg2d_n2^21_d32", "rmat24_ef16", "chunglu_batch4096")
+OFFSETS64 = {"rmat24_ef16"}
+# bounded CPU sample of the headline's generator for the oracle timings
+CPU_SAMPLE = dict(scale=15, edge_factor=16, seed=4)
+CPU_SAMPLE_DESC = ("oracle (serial Algorithm 1 peel, 1 core, support included) on R-MAT scale 15, edge "
+                   "factor 16, a/b/c/d=.57/.19/.19/.05, seed 4: the headline's generator at 1/512 of its size")
 
 
 def dist_info():
@@ -184,8 +203,7 @@ def peaks():
 
 def cpu_sample_graph():
     import graphgen as gg
-    return gg.chung_lu(CPU_SAMPLE["n"], CPU_SAMPLE["gamma"], CPU_SAMPLE["mean_deg"], CPU_SAMPLE["max_deg"],
-                       CPU_SAMPLE["seed"])
+    return gg.rmat(CPU_SAMPLE["scale"], CPU_SAMPLE["edge_factor"], seed=CPU_SAMPLE["seed"])
 
 
 def time_oracle_once(g):
@@ -221,7 +239,7 @@ def run_reference(args):
     emit({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
           "warmup": args.warmup, "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-          "config": {"workload": f"{args.workload}: {WORKLOAD_DESC}",
+          "config": {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, args.workload)}",
                      "sample": f"each step: {CPU_SAMPLE_DESC}", "m_sample": m},
           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE_DESC},
           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
@@ -230,42 +248,75 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 
-CALIB_SEEDS = (101, 102)
 VARIANTS = {}
 VARIANT_DESC = {"learned": "learned cost model per sub-level (heuristic below 64 light edges)",
                 "heuristic": "fixed per-sub-level heuristic", "thread": "thread per light edge",
                 "group": "half a warp per light edge", "warp": "warp per light edge"}
 
 
-def calibrate(pkt, workload, seeds, repeats=2, epochs=2000):
-    """Trains the sub-level cost model (untimed) on other graphs of the
-    workload's family and size: each is decomposed under every light-edge
-    variant with tracing, and the device trainer fits the measured times."""
+def calibration_graphs(gg):
+    """Other members of the workloads' families (seed 101), the scheduler's
+    training graphs; the R-MAT family enters at scale 21."""
+    return [("rmat10_ef8 seed 101", gg.workload("rmat10_ef8", 101)),
+            ("chunglu_n2^20_d20 seed 101", gg.workload("chunglu_n2^20_d20", 101)),
+            ("rgg2d_n2^21_d32 seed 101", gg.workload("rgg2d_n2^21_d32", 101)),
+            ("R-MAT scale 21 edge factor 16 seed 101", gg.rmat(21, 16, seed=101))]
+
+
+def calibrate(pkt, repeats=2, epochs=2000):
+    """Trains the sub-level cost model (untimed): each calibration graph is
+    decomposed under every variant with tracing, and the device trainer fits
+    the measured times."""
     import numpy as np
     import torch
 
     import graphgen as gg
 
     t0 = time.perf_counter()
-    xs, ys = [], []
-    for s in seeds:
-        c = gg.workload(workload, seed=s)
+    xs, ys, names = [], [], []
+    for name, c in calibration_graphs(gg):
         Gc = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n)
         x, y = pkt.sched_dataset(Gc, repeats=repeats)
         Gc.free()
         xs.append(x)
         ys.append(y)
+        names.append(name)
     X = torch.from_numpy(np.concatenate(xs)).cuda()
     Y = torch.from_numpy(np.concatenate(ys)).cuda()
     params = pkt.sched_init(seed=0)
     loss = pkt.sched_train(params, X, Y, epochs=epochs, lr=3e-3)
     torch.cuda.synchronize()
-    return params, {"graphs": [f"{workload} seed {s}" for s in seeds], "samples": int(X.shape[0]),
-                    "epochs": epochs, "mse_log2_ns": loss, "seconds": round(time.perf_counter() - t0, 2)}
+    return params, {"graphs": names, "samples": int(X.shape[0]), "epochs": epochs, "mse_log2_ns": loss,
+                    "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def phase_record(st, n, ms_sup, ms_peel, peak):
+    """Each phase's algorithmic bytes over its device time against the peak."""
+    b_sup, b_peel = algorithmic_bytes(st, n)
+    out = {}
+    for name, b, ms in (("support", b_sup, ms_sup), ("peel", b_peel, ms_peel)):
+        ach = b / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+        out[name] = {"ms": ms, "algorithmic_bytes": b, "achieved_gbs": ach, "frac": ach / peak}
+    return out
+
+
+def form_record(per, stats):
+    return {"ms_per_step": statistics.mean(per), "steps": len(per),
+            "ms_support": statistics.mean(s["ms_support"] for s in stats),
+            "ms_peel": statistics.mean(s["ms_peel"] for s in stats),
+            "launches_per_step": int(statistics.mean(s["launches"] for s in stats))}
+
+
+def ratios(rec):
+    out = {}
+    lm = rec["forms"]["learned"]["ms_per_step"]
+    for other in ("plain", "heuristic", "graph"):
+        if other in rec["forms"]:
+            out[f"learned_over_{other}"] = rec["forms"][other]["ms_per_step"] / lm
+    return out
 
 
 def run_gpu(args):
-    import numpy as np
     import torch
 
     import graphgen as gg
@@ -287,21 +338,18 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    g = gg.workload(args.workload)
-    src = torch.from_numpy(g.src).cuda()
-    dst = torch.from_numpy(g.dst).cuda()
-    G = pkt.build_csr(src, dst, g.n)
-    m = G.m
-    out = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = peaks()
     loop = {"persistent": pkt.LOOP_PERSISTENT, "plain": pkt.LOOP_PLAIN, "graph": pkt.LOOP_GRAPH}[args.loop]
     variant = VARIANTS[args.variant]
-    stream = torch.cuda.current_stream()
     params, calib = None, None
-    if args.variant == "learned":
-        params, calib = calibrate(pkt, args.workload, CALIB_SEEDS)
+    if args.variant == "learned" or not args.no_configs:
+        params, calib = calibrate(pkt)
+    forms = {"plain": (pkt.LOOP_PLAIN, pkt.VAR_AUTO), "heuristic": (pkt.LOOP_PERSISTENT, pkt.VAR_AUTO),
+             "learned": (pkt.LOOP_PERSISTENT, pkt.VAR_LEARNED), "graph": (pkt.LOOP_GRAPH, pkt.VAR_AUTO)}
 
-    def timed(loop_form, var, steps, warmup, sched=None):
+    def timed(G, out, loop_form, var, steps, warmup, sched=None):
         for _ in range(warmup):
             G.decompose(out=out, loop=loop_form, variant=var, sync=True, stats=True, sched_params=sched)
         barrier()
@@ -319,24 +367,59 @@ def run_gpu(args):
         barrier()
         return per, stats
 
+    def batch_timed(graphs, loop_form, var, steps, warmup, sched=None):
+        # each call unions, builds and decomposes; the device times of its
+        # support and peel phases are the step
+        per, stats = [], []
+        for i in range(warmup + steps):
+            flush.zero_()
+            _, st = pkt.decompose_batch(graphs, loop=loop_form, variant=var, stats=True, sched_params=sched)
+            if i >= warmup:
+                per.append(st["ms_support"] + st["ms_peel"])
+                stats.append(st)
+        return per, stats
+
+    def config_entry(name, n, m, results):
+        rec = {"workload": WORKLOAD_DESC.get(name, name), "n": n, "m": m,
+               "forms": {k: form_record(*v) for k, v in results.items()}}
+        if "learned" in results:
+            rec.update(ratios(rec))
+            st = results["learned"][1][-1]
+            f = rec["forms"]["learned"]
+            rec["phases"] = phase_record(st, n, f["ms_support"], f["ms_peel"], peak)
+            rec["triangles"], rec["t_max"], rec["sublevels"] = st["triangles"], st["t_max"], st["sublevels"]
+        return rec
+
+    # ---- the headline workload
+    g = gg.workload(args.workload)
+    off64 = args.workload in OFFSETS64
+    G = pkt.build_csr(torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(), g.n, offsets64=off64)
+    m = G.m
+    out = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
     with ClockSampler(local) as clk:
-        per, stats = timed(loop, variant, args.steps, args.warmup, params)
+        per, stats = timed(G, out, loop, variant, args.steps, args.warmup, params)
     value, total_ms = whole_job(sum(per), m, args.steps, dist, device="cuda")
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
     st0 = stats[-1]
-    res["config"] = {"workload": f"{args.workload}: {WORKLOAD_DESC}", "m": m, "n": g.n,
-                     "loop": args.loop, "variant": VARIANT_DESC[args.variant], "vertex_order": "degree",
-                     "l2": "flushed between steps (256 MiB write, untimed)", "replicas": ws,
-                     "triangles": st0["triangles"], "t_max": st0["t_max"], "sublevels": st0["sublevels"],
-                     "scans": st0["scans"], "scanned_entries": st0["scanned"]}
+    res["config"] = {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, args.workload)}",
+                     "m": m, "n": g.n, "loop": args.loop, "variant": VARIANT_DESC[args.variant],
+                     "vertex_order": "degree", "row_offsets": "int64" if off64 else "int32",
+                     "l2": "flushed between steps (256 MiB write, untimed); inputs also exceed L2",
+                     "preprocessing": ("CSR build and the per-graph peel workspace (row records, hub bitmaps, "
+                                       "min-degree table) are built before the timed steps (the workspace by "
+                                       "the first warm-up decomposition); the e2e leg includes both"),
+                     "replicas": ws, "triangles": st0["triangles"], "t_max": st0["t_max"],
+                     "sublevels": st0["sublevels"], "scans": st0["scans"], "scanned_entries": st0["scanned"],
+                     "dmin_sum": st0["dmin_sum"], "wedges_up": st0["wedges_up"]}
     if calib is not None:
         res["config"]["scheduler_calibration"] = calib
     # the paper's own rate: wedges |^| = sum_v d(v)(d(v)-1)/2 per second
     rowptr = G.csr()[0].to(torch.int64)
     deg = rowptr[1:] - rowptr[:-1]
     wedges = int((deg * (deg - 1) // 2).sum().item())
+    del rowptr, deg
     res["config"]["wedges"] = wedges
     res["config"]["gweps"] = wedges / (total_ms / args.steps / 1000.0) / 1e9
     res["gpu_launches"] = int(sum(s["launches"] for s in stats))
@@ -346,7 +429,6 @@ def run_gpu(args):
     ms_sup = statistics.mean(s["ms_support"] for s in stats)
     ms_peel = statistics.mean(s["ms_peel"] for s in stats)
     b_sup, b_peel = algorithmic_bytes(st0, g.n)
-    peak, peak_kind = peaks()
     if ms_peel >= ms_sup:
         kname = {"persistent": "k_persistent", "plain": "k_process", "graph": "k_gprocess"}[args.loop]
         b, ms = b_peel, ms_peel
@@ -360,26 +442,22 @@ def run_gpu(args):
                        "phases_ms": {"support": ms_sup, "peel": ms_peel},
                        "algorithmic_bytes": {"support": b_sup, "peel": b_peel}}
 
+    configs = {}
     if not args.no_plain:
-        # the other forms on the same graph: the host-driven loop with the
-        # fixed heuristic (the baseline form), the graph-driven loop and,
-        # when the reported form is learned, the persistent loop with the
-        # fixed heuristic
-        k = max(3, min(args.steps, 5))
-        others = {}
-        if args.loop != "plain" or args.variant != "heuristic":
-            others["plain"] = (pkt.LOOP_PLAIN, pkt.VAR_AUTO)
-        if args.loop == "persistent" and args.variant != "heuristic":
-            others["persistent_heuristic"] = (pkt.LOOP_PERSISTENT, pkt.VAR_AUTO)
-        if args.loop != "graph":
-            others["graph"] = (pkt.LOOP_GRAPH, pkt.VAR_AUTO)
-        for name, (lf, vf) in others.items():
-            pper, pstats = timed(lf, vf, k, 3)
-            pv = m / (statistics.mean(pper) / 1000.0) * ws
-            res[name] = {"value": pv, "unit": UNIT, "ms_per_step": statistics.mean(pper), "steps": k,
-                         "speedup_of_reported_form": value / pv,
-                         "ms_peel": statistics.mean(s["ms_peel"] for s in pstats),
-                         "launches_per_step": int(statistics.mean(s["launches"] for s in pstats))}
+        # the other level-loop forms on the headline graph (fewer steps)
+        key = {("persistent", "learned"): "learned", ("persistent", "heuristic"): "heuristic",
+               ("plain", "heuristic"): "plain", ("graph", "heuristic"): "graph"}.get((args.loop, args.variant),
+                                                                                      "reported")
+        head = {key: (per, stats)}
+        k = args.side_steps
+        for name, (lf, vf) in forms.items():
+            if name in head or (name == "graph" and args.workload in OFFSETS64 and not args.graph_on_large):
+                continue
+            head[name] = timed(G, out, lf, vf, k, 1, params)
+        configs[args.workload] = config_entry(args.workload, g.n, m, head)
+    G.free()
+    del out
+    torch.cuda.empty_cache()
 
     if not args.no_e2e:
         # the public host-buffer entry point: H2D of the raw edge list from
@@ -388,18 +466,54 @@ def run_gpu(args):
         hd = torch.from_numpy(g.dst).pin_memory()
         ho = torch.empty(g.n_in, dtype=torch.int32).pin_memory()
         hs_np, hd_np, ho_np = hs.numpy(), hd.numpy(), ho.numpy()
-        pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop, variant=variant, sched_params=params)
+        pkt.decompose_host(hs_np, hd_np, g.n, offsets64=off64, out=ho_np, loop=loop, variant=variant,
+                           sched_params=params)
         barrier()
-        k = max(1, min(args.steps, 5))
+        k = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
         for _ in range(k):
-            tau, _ = pkt.decompose_host(hs_np, hd_np, g.n, out=ho_np, loop=loop, variant=variant,
-                                        sched_params=params)
+            pkt.decompose_host(hs_np, hd_np, g.n, offsets64=off64, out=ho_np, loop=loop, variant=variant,
+                               sched_params=params)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / k
         res["e2e"] = {"value": m / dt * ws, "unit": UNIT, "h2d_bytes_per_step": int(8 * g.n_in),
-                      "d2h_bytes_per_step": int(4 * m), "ms_per_step": dt * 1000,
-                      "includes": "H2D of raw pairs, device CSR build, support, peel, D2H of trussness"}
+                      "d2h_bytes_per_step": int(4 * m), "ms_per_step": dt * 1000, "steps": k,
+                      "includes": ("H2D of raw pairs, device CSR build, peel workspace, support, peel, "
+                                   "D2H of trussness")}
+        del hs, hd, ho
+    del g
+
+    if not args.no_configs:
+        ks, kw = args.config_steps, 3
+        for name in CONFIG_WORKLOADS:
+            if name in configs or name == args.workload:
+                continue
+            if name == "chunglu_batch4096":
+                graphs = gg.chung_lu_batch(4096)
+                n_all = sum(x.n for x in graphs)
+                results = {f: batch_timed(graphs, lf, vf, 3, 1, params) for f, (lf, vf) in forms.items()}
+                configs[name] = config_entry(name, n_all, int(results["learned"][1][-1]["m"]), results)
+                del graphs
+                continue
+            c = gg.workload(name)
+            Gc = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n,
+                               offsets64=name in OFFSETS64)
+            oc = torch.empty(max(Gc.m, 1), dtype=torch.int32, device="cuda")
+            results = {f: timed(Gc, oc, lf, vf, ks, kw, params) for f, (lf, vf) in forms.items()}
+            configs[name] = config_entry(name, c.n, Gc.m, results)
+            Gc.free()
+            del oc, c
+    if configs:
+        for i, name in enumerate(CONFIG_WORKLOADS):
+            if name in configs:
+                configs[name]["config_index"] = i + 1
+        res["configs"] = configs
+        res["targets"] = {
+            "learned_over_plain_ge_1.5_on_cfg1_4": {
+                nm: configs[nm].get("learned_over_plain") for nm in CONFIG_WORKLOADS[:4] if nm in configs},
+            "cfg3_phases_ge_0.30_of_hbm_peak": (
+                {ph: configs["rgg2d_n2^21_d32"]["phases"][ph]["frac"] for ph in ("support", "peel")}
+                if "rgg2d_n2^21_d32" in configs and "phases" in configs["rgg2d_n2^21_d32"] else None)}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline()
@@ -408,20 +522,24 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         emit(res)
-    G.free()
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[w for w in WORKLOAD_DESC if w != "chunglu_batch4096"])
     ap.add_argument("--loop", default="persistent", choices=["persistent", "plain", "graph"])
     ap.add_argument("--variant", default="learned", choices=sorted(VARIANT_DESC))
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--side-steps", type=int, default=3, help="timed steps of the other forms on the headline graph")
+    ap.add_argument("--config-steps", type=int, default=5, help="timed steps per form on the other workloads")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--graph-on-large", action="store_true", help="also time the graph-driven loop on R-MAT 24")
+    ap.add_argument("--no-plain", action="store_true", help="skip the other forms on the headline graph")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-workload block")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
