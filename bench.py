@@ -154,10 +154,15 @@ def algorithmic_bytes(st, n):
     library: support = 32m + 8n + 4W+ + 12T; peeling = (16 V - 8m) for the
     Scans (V = entries visited: an 8-byte support/stamp read per entry, plus
     a 4-byte id read and a 4-byte survivor write after the first Scan) +
-    36m + 4 sum_e min(d(u), d(v)) + 28T."""
+    36m + 4 X + 28T + 24 C, where X = the shorter-row entries walked (the
+    sum of min(d(u), d(v)) over the rows as they stood when each edge was
+    peeled: compaction drops processed edges from them) and C = the row
+    entries the compactions visited (4-byte neighbour, 4-byte id and 8-byte
+    support/stamp read, 8 bytes written per entry at most)."""
     m, T = st["m"], st["triangles"]
     sup = 32 * m + 8 * n + 4 * st["wedges_up"] + 12 * T
-    peel = (16 * st["scanned"] - 8 * m) + 36 * m + 4 * st["dmin_sum"] + 28 * T
+    walked = st.get("walked", st["dmin_sum"])
+    peel = (16 * st["scanned"] - 8 * m) + 36 * m + 4 * walked + 28 * T + 24 * st.get("compacted_slots", 0)
     return sup, peel
 
 
@@ -412,7 +417,8 @@ def run_gpu(args):
                                        "the first warm-up decomposition); the e2e leg includes both"),
                      "replicas": ws, "triangles": st0["triangles"], "t_max": st0["t_max"],
                      "sublevels": st0["sublevels"], "scans": st0["scans"], "scanned_entries": st0["scanned"],
-                     "dmin_sum": st0["dmin_sum"], "wedges_up": st0["wedges_up"]}
+                     "dmin_sum": st0["dmin_sum"], "walked": st0["walked"], "compactions": st0["compactions"],
+                     "compacted_slots": st0["compacted_slots"], "wedges_up": st0["wedges_up"]}
     if calib is not None:
         res["config"]["scheduler_calibration"] = calib
     # the paper's own rate: wedges |^| = sum_v d(v)(d(v)-1)/2 per second

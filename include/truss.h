@@ -128,6 +128,20 @@ TRUSS_API int truss_csr_copy(const truss_graph* g, int64_t* d_rowptr, int32_t* d
  */
 TRUSS_API int truss_support(truss_graph* g, int32_t* d_support, void* stream);
 
+/*
+ * truss_support_ros -- the same S(e) by the edge-centric scheme of
+ * Algorithm 2 (Ros's support step, §II): each edge {u, v} counts, on its
+ * own, the neighbours of v that are also neighbours of u -- here by walking
+ * the shorter of the two rows and searching each entry in the longer one
+ * (the hub bitmap of a high-degree vertex stands in for the marker array X).
+ * No orientation and no atomics: every edge writes its own count, at the
+ * cost of min(d(u), d(v)) searches per edge instead of the oriented
+ * scheme's one search per wedge of N+ lists.
+ *   d_support : device int32[m], canonical order (written).
+ * Allocates the graph's peeling workspace on first use, like truss_decompose.
+ */
+TRUSS_API int truss_support_ros(truss_graph* g, int32_t* d_support, void* stream);
+
 /* ------------------------------------------------------- decomposition */
 
 /* level-loop forms (how the sub-levels of Algorithm 4 are driven) */
@@ -230,7 +244,26 @@ typedef struct truss_opts {
                              TRUSS_VAR_LEARNED, or NULL                      */
     const int8_t* tune_table;  /* host int8[TRUSS_TUNE_CLASSES] consulted by
                              TRUSS_VAR_AUTO, or NULL (built-in default)      */
+    int32_t compact;      /* row compaction between levels (persistent and
+                             plain loops): -1 automatic (graphs of at least
+                             TRUSS_COMPACT_MIN_EDGES edges), 0 off, 1 on for
+                             any size.  Once at most half of the edges the
+                             rows hold are unprocessed, the entries of
+                             processed edges are dropped from the rows, so
+                             ProcessSubLevel walks and searches only live
+                             rows (the triangles it skips are those through
+                             processed edges, §III); results are identical */
+    int32_t max_level;    /* capacity (levels) of the two arrays below        */
+    int64_t* h_level_edges; /* optional host int64[max_level]: edges peeled at
+                             support level l, i.e. of trussness l + 2 (the
+                             trussness distribution of Fig. 6); needs sync  */
+    int64_t* h_level_ns;  /* optional host int64[max_level]: device time of
+                             level l -- its Scans and sub-levels (the time
+                             distribution of Fig. 6); needs sync = 1        */
 } truss_opts;
+
+/* Graphs with at least this many edges compact their rows by default. */
+#define TRUSS_COMPACT_MIN_EDGES 65536
 
 typedef struct truss_stats {
     int64_t m;           /* undirected edges                                 */
@@ -253,7 +286,12 @@ typedef struct truss_stats {
     int32_t blocks_per_sm; /* its blocks per SM (4: _LAT form, 6: _OCC)      */
     int32_t max_support; /* largest support before peeling (set when stats
                             are requested or the form is chosen)           */
-    int32_t reserved;
+    int32_t compactions; /* row compactions the peel ran (sync = 1)          */
+    int64_t walked;      /* shorter-row entries ProcessSubLevel walked: the
+                            sum over sub-levels of the frontier's shorter-row
+                            lengths as the rows stood then (dmin_sum without
+                            compaction; sync = 1)                           */
+    int64_t compacted_slots; /* row entries the compactions visited (sync)  */
 } truss_stats;
 
 /*
@@ -313,6 +351,27 @@ TRUSS_API void truss_default_opts(truss_opts* opts);
 TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts* opts, truss_stats* stats, void* stream);
 
 /*
+ * truss_decompose_local -- the same trussness by the asynchronous local
+ * iteration the paper contrasts with level-synchronous peeling (§II: the
+ * MPM-style update rule and its nucleus/truss generalisation).  Starting
+ * from S(e) + 2, every active edge repeatedly takes the value
+ *   2 + min(its value - 2, h),  h = the largest k such that at least k of
+ *   its triangles {e, e2, e3} have min(value(e2), value(e3)) - 2 >= k,
+ * in place and without level or sub-level barriers, until a sweep changes
+ * nothing; edges sharing a triangle with a changed edge are the next sweep's
+ * active set.  The fixed point reached from these upper bounds is the
+ * trussness, identical to truss_decompose.
+ *   d_truss    : device int32[m], canonical order (written).
+ *   max_sweeps : limit on sweeps (<= 0: none); TRUSS_ETIMEOUT when reached.
+ *   h_sweeps, h_updates : may be NULL; receive the sweeps run and the value
+ *                changes made.
+ * Synchronises `stream` once per sweep.  Allocates 6 bytes per edge for the
+ * call, and the graph's peeling workspace on first use.
+ */
+TRUSS_API int truss_decompose_local(truss_graph* g, int32_t* d_truss, int64_t max_sweeps, int64_t* h_sweeps,
+                                    int64_t* h_updates, void* stream);
+
+/*
  * truss_peel_sublevel -- one ProcessSubLevel (Algorithm 5) on a caller-set
  * state, for tests and tuning.  All arrays are device arrays in canonical
  * edge order:
@@ -323,7 +382,9 @@ TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts
  *             in-curr bit is set by the call);
  *   d_next  : int32[m] receives the next frontier (any order);
  *   h_nnext : host int64, receives |next|.
- * Synchronises `stream`.
+ * Synchronises `stream`.  TRUSS_EINVAL when ncurr > m.  d_curr is checked
+ * on the device before any other kernel reads it: TRUSS_EBADGRAPH when an id
+ * lies outside [0, m) or appears twice (the state is then left untouched).
  */
 TRUSS_API int truss_peel_sublevel(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr, int64_t ncurr,
                         int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant, void* stream);
@@ -425,17 +486,26 @@ TRUSS_API int truss_sync(truss_graph* g, void* stream);
  *   n, m     : vertices (0 <= n <= TRUSS_NOALLOC_MAX_VERTICES) and edges.
  *   d_support: device int32[m], indexed by edge id (written).
  * Scratch: a fixed array of (TRUSS_NOALLOC_MAX_VERTICES + 64) int32 (16 MiB)
- * in the library's device memory, held by every GPU that loads the library
- * until the process exits.  The first call on each device looks up that
- * array's address (cudaGetSymbolAddress, with the device current) and caches
- * it; make that first call before any stream capture.  All calls share the
- * array, so calls whose device work overlaps (on two streams, or from two
- * host threads) race and must be serialised by the caller.
+ * in the library's device memory, held by every GPU that uses it until the
+ * process exits.  CUDA loads the library's device code lazily, so the array
+ * is reserved on a device by the first truss_support_noalloc call there
+ * (which can fail with TRUSS_ENOMEM or TRUSS_ECUDA if device memory is
+ * already exhausted); that call also looks up the array's address
+ * (cudaGetSymbolAddress, with the device current) and caches it.  A caller
+ * whose allocator will take all device memory should therefore make one call
+ * first -- a call with n = 0 and m = 0 does only this set-up -- and make it
+ * before any stream capture.  All calls share the array, so calls whose
+ * device work overlaps (on two streams, or from two host threads) race and
+ * must be serialised by the caller.
+ * Checks: d_rowptr is validated on the device before any other array is read
+ * through it (d_rowptr[0] = 0, d_rowptr[n] = 2m, no row ends before it
+ * starts); neighbours and edge ids are range-checked where they are used.
  * Synchronises `stream`.  Returns TRUSS_ETOOBIG when n exceeds the maximum,
- * TRUSS_EBADGRAPH when the kernel met a neighbour or edge id out of range
+ * TRUSS_EOVERFLOW when 2m exceeds INT32_MAX, TRUSS_EBADGRAPH for bad row
+ * offsets (nothing else is read) or a neighbour or edge id out of range
  * (those entries are skipped, never written through), TRUSS_EINVAL for null
- * pointers or negative sizes.  Rows that are not sorted, or offsets outside
- * [0, 2m], are not detected.
+ * pointers or negative sizes.  Rows that are not sorted are not detected;
+ * they give wrong counts but every access stays within the arrays.
  */
 TRUSS_API int truss_support_noalloc(const int32_t* d_rowptr, const int32_t* d_col, const int32_t* d_eid, int32_t n,
                                     int64_t m, int32_t* d_support, void* stream);

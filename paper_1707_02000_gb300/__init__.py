@@ -40,7 +40,7 @@ EXPORTS = (
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
     "truss_decompose_batch", "truss_sched_features", "truss_sched_init", "truss_sched_grad",
     "truss_sched_train", "truss_sched_predict", "truss_autotune", "truss_ktruss_components",
-    "truss_triangle_count",
+    "truss_triangle_count", "truss_support_ros", "truss_decompose_local",
 )
 
 
@@ -56,7 +56,8 @@ class Opts(ctypes.Structure):
                 ("h_sub_level", ctypes.POINTER(ctypes.c_int32)), ("h_sub_size", ctypes.POINTER(ctypes.c_int64)),
                 ("max_sub", ctypes.c_int64), ("d_peel_step", ctypes.c_void_p),
                 ("h_trace", ctypes.c_void_p), ("sched_params", ctypes.c_void_p),
-                ("tune_table", ctypes.c_void_p)]
+                ("tune_table", ctypes.c_void_p), ("compact", ctypes.c_int32), ("max_level", ctypes.c_int32),
+                ("h_level_edges", ctypes.c_void_p), ("h_level_ns", ctypes.c_void_p)]
 
 
 # truss_sublevel_trace, one record per sub-level
@@ -71,10 +72,11 @@ class Stats(ctypes.Structure):
                 ("ms_support", ctypes.c_float), ("ms_peel", ctypes.c_float), ("launches", ctypes.c_int64),
                 ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("scanned", ctypes.c_int64),
                 ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("max_support", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_support", ctypes.c_int32), ("compactions", ctypes.c_int32), ("walked", ctypes.c_int64),
+                ("compacted_slots", ctypes.c_int64)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def _declare(lib):
@@ -90,6 +92,8 @@ def _declare(lib):
     lib.truss_edge_list.argtypes = [vp, vp, vp, vp]
     lib.truss_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.truss_support.argtypes = [vp, vp, vp]
+    lib.truss_support_ros.argtypes = [vp, vp, vp]
+    lib.truss_decompose_local.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     lib.truss_ktruss_components.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.truss_triangle_count.argtypes = [vp, vp, vp]
     lib.truss_default_opts.argtypes = [ctypes.POINTER(Opts)]
@@ -230,15 +234,26 @@ class Graph:
 
     def decompose(self, out=None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, sync=True, level_jump=True,
                   timeout_ns=10_000_000_000, record=False, max_sub=1 << 20, stream=None, stats=False,
-                  peel_step=None, trace=False, sched_params=None, tune_table=None):
+                  peel_step=None, trace=False, sched_params=None, tune_table=None, compact=-1,
+                  level_hist=False, max_level=1 << 16):
         """Trussness (int32[m], canonical order).  With ``record`` also
         returns the (level, |curr|) of every sub-level; with ``trace`` a
         structured array (TRACE_DTYPE) with one record per sub-level; with
-        ``stats`` a dict of run statistics; ``peel_step`` (a CUDA int32[m]
-        tensor) receives the sub-level each edge was peeled in."""
+        ``level_hist`` a pair of int64 arrays (edges peeled, device ns) per
+        support level 0..t_max-2; with ``stats`` a dict of run statistics;
+        ``peel_step`` (a CUDA int32[m] tensor) receives the sub-level each
+        edge was peeled in; ``compact`` selects row compaction (-1 automatic,
+        0 off, 1 on)."""
         out = self._empty(self.m) if out is None else out
-        o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record or trace)),
-                         level_jump=int(bool(level_jump)), timeout_ns=timeout_ns)
+        o = default_opts(loop=loop, variant=variant, sync=int(bool(sync or record or trace or level_hist)),
+                         level_jump=int(bool(level_jump)), timeout_ns=timeout_ns, compact=compact)
+        hl = hn = None
+        if level_hist:
+            hl = np.zeros(max_level, np.int64)
+            hn = np.zeros(max_level, np.int64)
+            o.h_level_edges = hl.ctypes.data
+            o.h_level_ns = hn.ctypes.data
+            o.max_level = max_level
         tune_table = _policy(o, sched_params, tune_table)
         tr = None
         if trace:
@@ -263,6 +278,9 @@ class Graph:
             res.append((rl[:k].copy(), rs[:k].copy()))
         if trace:
             res.append(tr[: min(int(st.sublevels), max_sub)].copy())
+        if level_hist:
+            k = min(max(int(st.t_max) - 1, 0), max_level)
+            res.append((hl[:k].copy(), hn[:k].copy()))
         if stats:
             res.append(st.as_dict())
         return res[0] if len(res) == 1 else tuple(res)
@@ -277,6 +295,21 @@ class Graph:
                                         _dptr(nxt) if self.m else None, ctypes.byref(k), variant,
                                         _stream(stream)), "truss_peel_sublevel")
         return nxt[: k.value]
+
+    def support_ros(self, out=None, stream=None):
+        """S(e) by the edge-centric scheme of Algorithm 2 (canonical order)."""
+        out = self._empty(self.m) if out is None else out
+        _check(_lib.truss_support_ros(self._h, _dptr(out) if self.m else None, _stream(stream)), "truss_support_ros")
+        return out
+
+    def decompose_local(self, out=None, max_sweeps: int = 0, stats: bool = False, stream=None):
+        """Trussness by the asynchronous local h-index iteration (canonical
+        order); with ``stats`` also {"sweeps", "updates"}."""
+        out = self._empty(self.m) if out is None else out
+        sw, up = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.truss_decompose_local(self._h, _dptr(out) if self.m else None, max_sweeps, ctypes.byref(sw),
+                                          ctypes.byref(up), _stream(stream)), "truss_decompose_local")
+        return (out, {"sweeps": int(sw.value), "updates": int(up.value)}) if stats else out
 
     def triangle_count(self, stream=None) -> int:
         """Number of triangles (each counted once)."""
@@ -323,7 +356,7 @@ def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = Fal
 
 def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool = True, offsets64: bool = False,
                    out: np.ndarray | None = None, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None,
-                   sched_params=None, tune_table=None):
+                   sched_params=None, tune_table=None, compact=-1):
     """Host arrays in, host trussness out (canonical order): the C ABI's
     truss_decompose_host.  ``src``/``dst`` should be pinned for speed."""
     src = np.ascontiguousarray(src, np.int32)
@@ -332,7 +365,7 @@ def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool 
     out = np.empty(max(cap, 1), np.int32) if out is None else out
     flags = (DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
     m = ctypes.c_int64()
-    o = default_opts(loop=loop, variant=variant, sync=1)
+    o = default_opts(loop=loop, variant=variant, sync=1, compact=compact)
     tune_table = _policy(o, sched_params, tune_table)
     st = Stats()
     _check(_lib.truss_decompose_host(src.ctypes.data_as(ctypes.c_void_p), dst.ctypes.data_as(ctypes.c_void_p),
@@ -343,7 +376,7 @@ def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool 
 
 
 def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, variant=VAR_AUTO, stream=None,
-                    stats: bool = False, sched_params=None, tune_table=None):
+                    stats: bool = False, sched_params=None, tune_table=None, compact=-1):
     """Decompose many independent graphs (objects with ``n``, ``src``,
     ``dst``; ids local to each graph) in one run on the device.  Returns the
     list of per-graph trussness arrays (CUDA tensors, canonical order of
@@ -359,7 +392,7 @@ def decompose_batch(graphs, degree_order: bool = True, loop=LOOP_PERSISTENT, var
     cap = int(eoff[-1])
     out = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
     moff = np.zeros(G + 1, np.int64)
-    o = default_opts(loop=loop, variant=variant, sync=1)
+    o = default_opts(loop=loop, variant=variant, sync=1, compact=compact)
     tune_table = _policy(o, sched_params, tune_table)
     st = Stats()
     _check(_lib.truss_decompose_batch(_dptr(src) if cap else None, _dptr(dst) if cap else None,

@@ -33,6 +33,17 @@
 //   hub_bits          per hub: 32-byte blocks of 192 vertex ids, {count of
 //                     neighbours before the block, 3 x 64 neighbour bits}
 //   ctr    int[...]   device counters (see peel.cu)
+// Row compaction (peel.cu; allocated on the first decomposition that uses it):
+//   wcol, weid int32[2m]  working copy of the rows; between levels the
+//                     entries of processed edges are dropped from it, so the
+//                     rows the peel walks and searches shrink as it goes
+//   tcol, teid int32[m]   scatter target of a compaction (a compaction runs
+//                     once at most half of the held edges are live, so the
+//                     live entries fit in m slots)
+//   wrows, wdmin, wlhub   working copies of rows / dmin / lhub, rewritten
+//                     for the live edges by each compaction
+//   vstart, vend Off[n]  current row bounds of every vertex in wcol
+//   cbits, ctoff, cbsum  live bits per slot, per-tile and per-block offsets
 #pragma once
 #include "common.cuh"
 
@@ -84,6 +95,16 @@ struct truss_graph {
     int32_t* live[2] = {nullptr, nullptr};  // live-edge lists of consecutive Scans
     int2* owner[2] = {nullptr, nullptr};     // chunk -> {edge, chunk index in its row}, per side
     uint32_t ocap = 0;
+    // row compaction (see peel.cu)
+    int32_t *wcol = nullptr, *weid = nullptr, *tcol = nullptr, *teid = nullptr;
+    void* wrows = nullptr;
+    int32_t *wdmin = nullptr, *wlhub = nullptr;
+    void *vstart = nullptr, *vend = nullptr;
+    uint32_t* cbits = nullptr;
+    int32_t* ctoff = nullptr;
+    long long* cbsum = nullptr;
+    int cmp_ready = 0;  // compaction workspace allocated
+    int cmp_dirty = 0;  // working copies may differ from the pristine arrays
     int* ctr = nullptr;
     int* h_ctr = nullptr;  // pinned host mirror
     int latched = 0;       // latched device-side error status

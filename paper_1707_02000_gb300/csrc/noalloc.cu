@@ -25,6 +25,20 @@ constexpr int NA_WARPS = 8;
 constexpr int NA_CAP = 256;  // N+(u) staged in shared memory up to this length
 constexpr int64_t NA_ERR = TRUSS_NOALLOC_MAX_VERTICES;  // error word index
 
+// Checks the caller's row offsets before anything reads the other arrays
+// through them: rowptr[0] = 0, rowptr[n] = 2m and no row ends before it
+// starts, so every slot read later lies in [0, 2m).  Reads rowptr[0..n]
+// only; a violation sets *err.
+__global__ void k_na_check_rows(const int32_t* __restrict__ rowptr, int32_t n, int64_t m, int32_t* err) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = rowptr[u], b = rowptr[u + 1];
+        bool bad = b < a;
+        if (u == 0) bad |= a != 0;
+        if (u == n - 1) bad |= (int64_t)b != 2 * m;
+        if (bad) atomicExch(err, 1);
+    }
+}
+
 __global__ void k_na_zero(int32_t* __restrict__ S, int64_t m) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
         S[i] = 0;
@@ -158,13 +172,22 @@ extern "C" int truss_support_noalloc(const int32_t* d_rowptr, const int32_t* d_c
                                      int64_t m, int32_t* d_support, void* stream) {
     if (n < 0 || m < 0 || (n > 0 && !d_rowptr) || (m > 0 && (!d_col || !d_eid || !d_support))) return TRUSS_EINVAL;
     if (n > TRUSS_NOALLOC_MAX_VERTICES) return TRUSS_ETOOBIG;
-    if (m == 0 || n == 0) return TRUSS_OK;
+    if (2 * m > (int64_t)INT32_MAX) return TRUSS_EOVERFLOW;  // slots are int32 row offsets
+    // set-up first, so that a call with n = 0 does only the set-up
     int32_t* scratch = nullptr;
     TRY(scratch_address(&scratch));
+    if (n == 0) return m == 0 ? TRUSS_OK : TRUSS_EBADGRAPH;
     cudaStream_t s = (cudaStream_t)stream;
     int32_t* eo = scratch;
     int32_t* err = scratch + NA_ERR;
     CU(cudaMemsetAsync(err, 0, sizeof(int32_t), s));  // the array keeps the last call's contents
+    k_na_check_rows<<<grid_for(n, 256), 256, 0, s>>>(d_rowptr, n, m, err);
+    CU(cudaGetLastError());
+    int32_t h_bad = 0;
+    CU(cudaMemcpyAsync(&h_bad, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h_bad) return TRUSS_EBADGRAPH;  // nothing was read through the offsets
+    if (m == 0) return TRUSS_OK;
     k_na_zero<<<grid_for(m, 256), 256, 0, s>>>(d_support, m);
     k_na_eo<<<grid_for(n, 256), 256, 0, s>>>(d_rowptr, d_col, n, eo);
     int dev = 0, sms = 0;

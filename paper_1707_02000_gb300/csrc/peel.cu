@@ -47,6 +47,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "rows.cuh"
 #include "sched.cuh"
 
 namespace {
@@ -61,8 +62,20 @@ enum {
     C_LAST_L = 38,
     C_TRI = 40,   // [40..41] triangle count (u64), [42] max support
     C_SCANNED = 44,  // [44..45] entries all Scans visited (i64)
-    C_TOTAL = 64
+    C_WALKED = 46,   // [46..47] shorter-row entries of all frontiers (i64)
+    C_ROS = 48,      // [48..49] next edge batch of the edge-centric support (u64)
+    C_ST = 64,       // [64..95] loop state a persistent launch leaves (PState)
+    C_TOTAL = 96
 };
+
+// Where a persistent launch stopped: at the end of the peel (stop = 0), or
+// before the Scan of level l when the rows are due for compaction (stop = 1;
+// the next launch resumes from here).
+struct PState {
+    int32_t l, g, stop, pad;
+    long long processed, nsub, sc, nlevel, nlive, scanned, walked, scan_ns;
+};
+static_assert(sizeof(PState) <= sizeof(int) * (C_TOTAL - C_ST), "PState fits the counter block");
 
 constexpr int PT = 256;      // threads per block in the peel kernels
 constexpr int PW = PT / 32;
@@ -130,22 +143,6 @@ __host__ __device__ __forceinline__ void clear_slot_vals(SlotVals* v) {
     v->nlive = 0;
 }
 
-template <typename Off>
-struct Graph {
-    const Off* __restrict__ rowptr;
-    const int32_t* __restrict__ col;
-    const int32_t* __restrict__ eid;
-    const int2* __restrict__ el;
-    const int32_t* __restrict__ dmin;  // min(d(u), d(v)) per edge
-    const Off* __restrict__ rows;      // per edge: shorter row [a0, a1), longer row [b0, b1)
-    const int32_t* __restrict__ lhub;  // per edge: hub index of the longer row's vertex, -1 if none
-    const unsigned long long* __restrict__ hbits;  // per hub: 32-byte blocks {count before, 3 x 64 ids}
-    int64_t hw;                                    // words per hub (4 per block)
-    int2* ss;
-    int64_t m;
-    int hc;  // heavy chunk length (entries of the shorter row)
-    uint32_t ocap;                     // capacity of each side's chunk owner map
-};
 
 __device__ __forceinline__ uint32_t nchunks_of(int d, int hc) { return (uint32_t)((d + hc - 1) / hc); }
 
@@ -320,73 +317,6 @@ __device__ __forceinline__ void on_triangles(int2* ss, int32_t e1, bool ok1, int
     if (d2y) settle(ss, y2, a2y, l, g, ap);
 }
 
-template <typename Off>
-struct Rows {
-    Off a0, a1, b0, b1;  // shorter row [a0, a1), longer row [b0, b1)
-    int32_t hub;         // hub index of the longer row's vertex, -1 if none
-};
-
-// The rows of edge e from its precomputed record (one 16-byte load for
-// int32 offsets, two for int64): no endpoint -> row-pointer round trip.
-template <typename Off>
-__device__ __forceinline__ Rows<Off> rows_of(const Graph<Off>& G, int32_t e) {
-    const int32_t hub = __ldg(G.lhub + e);
-    if constexpr (sizeof(Off) == 4) {
-        const int4 v = __ldg(reinterpret_cast<const int4*>(G.rows) + e);
-        return Rows<Off>{v.x, v.y, v.z, v.w, hub};
-    } else {
-        const longlong2* p = reinterpret_cast<const longlong2*>(G.rows) + 2 * (int64_t)e;
-        const longlong2 a = __ldg(p), b = __ldg(p + 1);
-        return Rows<Off>{a.x, a.y, b.x, b.y, hub};
-    }
-}
-
-// Slots of k1 and k2 in the ascending row a[lo, lo + n) (n >= 1), or -1.
-// Both searches run in lockstep (the step count depends on n only), so each
-// step issues two independent loads.  Each search keeps the last slot whose
-// value is <= its key, with that value, so no load follows the loop.
-template <typename Off>
-__device__ __forceinline__ void find2(const int32_t* __restrict__ a, Off lo, Off n, int32_t k1, int32_t k2, Off& p1,
-                                      Off& p2) {
-    Off b1 = lo, b2 = lo;
-    int32_t v1 = __ldg(a + lo), v2 = v1;
-    while (n > 1) {
-        const Off h = n >> 1;
-        const int32_t t1 = __ldg(a + b1 + h), t2 = __ldg(a + b2 + h);
-        if (t1 <= k1) {
-            b1 += h;
-            v1 = t1;
-        }
-        if (t2 <= k2) {
-            b2 += h;
-            v2 = t2;
-        }
-        n -= h;
-    }
-    p1 = v1 == k1 ? b1 : (Off)-1;
-    p2 = v2 == k2 ? b2 : (Off)-1;
-}
-
-// Slot of w in the row (starting at slot b0) of the vertex that owns hub h,
-// or -1.  The hub's bitmap is cut into 32-byte blocks of 192 ids: word 0
-// holds the number of neighbours before the block, words 1-3 the bits.  One
-// probe reads one block (one sector): the bit of w, and its rank = the count
-// before the block + the bits of the block's earlier words + the bits below
-// w in its word.
-template <typename Off>
-__device__ __forceinline__ Off hub_find(const Graph<Off>& G, int32_t h, Off b0, int32_t w) {
-    const int32_t b = w / 192, r = w - b * 192;
-    const ulonglong2* B = reinterpret_cast<const ulonglong2*>(G.hbits + (int64_t)h * G.hw + 4 * (int64_t)b);
-    const ulonglong2 lo = __ldg(B), hi = __ldg(B + 1);
-    const int k = r >> 6, bit = r & 63;
-    const unsigned long long word = k == 0 ? lo.y : (k == 1 ? hi.x : hi.y);
-    uint32_t rank = (uint32_t)lo.x;
-    if (k > 0) rank += (uint32_t)__popcll(lo.y);
-    if (k > 1) rank += (uint32_t)__popcll(hi.x);
-    rank += (uint32_t)__popcll(word & ((1ull << bit) - 1ull));
-    return ((word >> bit) & 1ull) ? b0 + (Off)rank : (Off)-1;
-}
-
 // All triangles through e1 whose apex is one of the slots start, start+step,
 // ... of [a0, a1) (part of the shorter row), each probed in the longer row;
 // a lane takes two slots at a time (j and j + step) and searches for both
@@ -407,7 +337,11 @@ __device__ __forceinline__ void walk_rows(const Graph<Off>& G, int32_t e1, Off a
             find2<Off>(G.col, r.b0, r.b1 - r.b0, w1, w2, q1, q2);
         }
         const bool ok1 = q1 >= 0, ok2 = two && q2 >= 0;
-        const int32_t y1 = ok1 ? __ldg(G.eid + q1) : 0, y2 = ok2 ? __ldg(G.eid + q2) : 0;
+        // a hub probe gives a slot of the row as built (the bitmaps are not
+        // rebuilt when rows are compacted; a stale bit finds a processed
+        // edge, whose triangle is skipped like any other)
+        const int32_t* ye = r.hub >= 0 ? G.oeid : G.eid;
+        const int32_t y1 = ok1 ? __ldg(ye + q1) : 0, y2 = ok2 ? __ldg(ye + q2) : 0;
         on_triangles(G.ss, e1, ok1, x1, y1, ok2, x2, y2, l, g, ap);
     }
 }
@@ -939,12 +873,6 @@ __device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns, un
     return s_ok != 0;
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // The whole of Algorithm 4 in one cooperative launch.  Every thread follows
 // the same (l, g, phase) sequence because every branch depends only on
 // counters read after a barrier.  Phase p (each Scan and each sub-level)
@@ -955,25 +883,46 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 // large frontiers of short rows need; 4 (64 registers, no spills) runs the
 // dependent-load chains of many small sub-levels of long rows fastest.
 // Measured on the power-law and geometric workloads against 5 and 7.
+// With `held` >= 0 the launch also stops (stop = 1) at the top of a level
+// once at most half of the `held` edges its rows hold are unprocessed (and
+// held >= min_held): the host then compacts the rows and resumes the loop
+// with `resume` set, from the state in the counter block.
 template <typename Off, int MINB>
 __global__ void __launch_bounds__(PT, MINB)
     k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
                  int level_jump, uint64_t timeout_ns, truss_sublevel_trace* trace, int64_t max_trace,
-                 const float* sched, TuneTable tt) {
+                 const float* sched, TuneTable tt, int64_t held, int64_t min_held, int resume) {
     __shared__ PeelSmem sm;
     __shared__ __align__(16) SlotVals sv;
     __shared__ int s_choice;
     smem_init(&sm);
     const unsigned nblocks = gridDim.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    PState* st = reinterpret_cast<PState*>(ctr + C_ST);
     unsigned epoch = 0;
     int32_t l = 0, g = 0;
     int64_t processed = 0, nsub = 0, sc = 0, nlevel = 0, p = 0;
     int64_t nlive = G.m;  // edges the next Scan visits
-    int64_t scanned = 0;
+    int64_t scanned = 0, walked = 0;
     uint64_t scan_ns = 0;
+    if (resume) {
+        l = st->l;
+        g = st->g;
+        processed = st->processed;
+        nsub = st->nsub;
+        sc = st->sc;
+        nlevel = st->nlevel;
+        nlive = st->nlive;
+        scanned = st->scanned;
+        walked = st->walked;
+        scan_ns = (uint64_t)st->scan_ns;
+    }
+    int stop = 0;
     while (processed < G.m) {
+        if (held >= min_held && 2 * (G.m - processed) <= held && processed > 0) {
+            stop = 1;  // the rows are due for compaction
+            break;
+        }
         uint64_t ts = 0;
         if (leader) {
             clear_slot_vals(slots(ctr) + ((p + 2) & 3));
@@ -1034,6 +983,7 @@ __global__ void __launch_bounds__(PT, MINB)
                 t0 = global_ns();
             }
             processed += nl + nh;
+            walked += (int64_t)v.dsum;
             const Frontier cu = (g & 1) ? f1 : f0;
             const Frontier nx = (g & 1) ? f0 : f1;
             const Appender ap{&sm, nx, slot_of(ctr, q), G.dmin, G.hc, G.ocap};
@@ -1049,12 +999,224 @@ __global__ void __launch_bounds__(PT, MINB)
         l++;
     }
     if (leader) {
+        st->l = l;
+        st->g = g;
+        st->stop = stop;
+        st->processed = processed;
+        st->nsub = nsub;
+        st->sc = sc;
+        st->nlevel = nlevel;
+        st->nlive = nlive;
+        st->scanned = scanned;
+        st->walked = walked;
+        st->scan_ns = (long long)scan_ns;
         ctr[C_NSUB] = (int)nsub;
         ctr[C_NSCAN] = (int)sc;
         ctr[C_NLEVEL] = (int)nlevel;
         ctr[C_LAST_L] = l;
         *reinterpret_cast<long long*>(ctr + C_SCANNED) = scanned;
+        *reinterpret_cast<long long*>(ctr + C_WALKED) = walked;
     }
+}
+
+// ------------------------------------------------------- row compaction
+//
+// A processed edge never takes part in a triangle again (Algorithm 5 skips
+// every triangle with a processed edge), so its two row entries can leave
+// the rows.  Between levels, once at most half of the edges the rows hold
+// are unprocessed, the live entries are packed into a second buffer (rows
+// keep their order and follow one another), every vertex gets its new row
+// bounds, and every live edge new records: its shorter live row (walked),
+// its longer live row (searched) and the walk length dmin, which also sets
+// its light / heavy class.  So ProcessSubLevel walks min(live d(u), live
+// d(v)) entries instead of min(d(u), d(v)), and searches shorter rows.
+// Four launches over the same grid:
+//   A  per tile of CT slots: the live bits, and the tile's offset within its
+//      block's contiguous range of tiles; per block, its live total;
+//   B  one block: exclusive prefix of the block totals;
+//   C  scatter the live entries; map each vertex's bounds through P(s), the
+//      number of live slots before slot s;
+//   D  the records of the live edges.
+// The hub bitmaps keep describing the rows as built: a longer row of a hub
+// that still holds more than 128 live entries is probed there, and the
+// probe's slot is read in the edge ids as built (a stale bit leads to a
+// processed edge, whose triangle is skipped).
+
+constexpr int CT = PT;        // slots per compaction tile (one per thread)
+constexpr int CTW = CT / 32;  // bit words per tile
+constexpr int CUN = 4;        // tiles per block step in phase A (loads in flight)
+
+template <typename Off>
+struct Compactor {
+    const int32_t* col;  // source rows (the rows as built, or the last compaction's)
+    const int32_t* eid;
+    int64_t nslots;      // source slots in use
+    int32_t* tcol;       // target rows
+    int32_t* teid;
+    Off* vstart;         // per vertex: row bounds in the target (updated in place)
+    Off* vend;
+    int first;           // the source is the rows as built (bounds from rowptr)
+    const Off* rowptr;
+    const int32_t* hub_of;  // per vertex: hub index, -1; nullptr without hubs
+    const int2* el;
+    const int2* ss;
+    int32_t g;           // sub-level number: processed <=> stamp < g
+    int32_t n;
+    Off* rows;           // working records
+    int32_t* dmin;
+    int32_t* lhub;
+    uint32_t* bits;      // one bit per source slot: its edge is live
+    int32_t* toff;       // per tile: live slots before it within its block's range
+    long long* bsum;     // per block: live total [0, B), then its offset [B, 2B)
+    int64_t live_slots;  // 2 x unprocessed edges: slots in the target
+};
+
+// block b of B takes tiles [nt b / B, nt (b + 1) / B)
+__host__ __device__ __forceinline__ int64_t tile_lo(int64_t nt, int64_t b, int64_t B) { return nt * b / B; }
+// the block whose range holds tile t
+__device__ __forceinline__ int64_t tile_owner(int64_t nt, int64_t t, int64_t B) { return ((t + 1) * B - 1) / nt; }
+
+template <typename Off>
+__global__ void __launch_bounds__(PT) k_cmp_count(Compactor<Off> C) {
+    __shared__ int wc[CUN][PW];
+    const int64_t nt = (C.nslots + CT - 1) / CT, B = gridDim.x;
+    const int64_t t0 = tile_lo(nt, blockIdx.x, B), t1 = tile_lo(nt, blockIdx.x + 1, B);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long carry = 0;  // thread 0's running total
+    for (int64_t t = t0; t < t1; t += CUN) {
+        int32_t e[CUN];
+#pragma unroll
+        for (int k = 0; k < CUN; k++) {
+            const int64_t s = (t + k) * CT + threadIdx.x;
+            e[k] = (t + k < t1 && s < C.nslots) ? __ldg(C.eid + s) : -1;
+        }
+        int st[CUN];
+#pragma unroll
+        for (int k = 0; k < CUN; k++) st[k] = e[k] >= 0 ? __ldg(&C.ss[e[k]].y) : -1;
+#pragma unroll
+        for (int k = 0; k < CUN; k++) {
+            const unsigned b = __ballot_sync(FULL_MASK, e[k] >= 0 && st[k] >= C.g);
+            if (t + k < t1) {
+                if (lane == 0) {
+                    C.bits[(t + k) * CTW + warp] = b;
+                    wc[k][warp] = __popc(b);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < CUN && t + k < t1; k++) {
+                C.toff[t + k] = (int32_t)carry;
+                for (int w = 0; w < PW; w++) carry += wc[k][w];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) C.bsum[blockIdx.x] = carry;
+}
+
+// one block: bsum[B + b] = sum of bsum[0, b)
+__global__ void k_cmp_blocks(long long* bsum, int B) {
+    __shared__ long long part[PT];
+    const int per = (B + PT - 1) / PT;
+    const int lo = min(B, (int)threadIdx.x * per), hi = min(B, lo + per);
+    long long s = 0;
+    for (int i = lo; i < hi; i++) s += bsum[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int i = 0; i < PT; i++) {
+            const long long v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (int i = lo; i < hi; i++) {
+        const long long v = bsum[i];
+        bsum[B + i] = run;
+        run += v;
+    }
+}
+
+// live slots before source slot s (0 <= s <= nslots)
+template <typename Off>
+__device__ __forceinline__ long long live_before(const Compactor<Off>& C, int64_t s, int64_t nt, int64_t B) {
+    if (s >= C.nslots) return C.live_slots;
+    const int64_t t = s / CT;
+    const int r = (int)(s - t * CT), w = r >> 5, bit = r & 31;
+    long long p = C.bsum[B + tile_owner(nt, t, B)] + C.toff[t];
+    const uint32_t* bw = C.bits + t * CTW;
+    for (int k = 0; k < w; k++) p += __popc(bw[k]);
+    return p + __popc(bw[w] & ((1u << bit) - 1u));
+}
+
+template <typename Off>
+__global__ void __launch_bounds__(PT) k_cmp_scatter(Compactor<Off> C) {
+    __shared__ long long base;
+    const int64_t nt = (C.nslots + CT - 1) / CT, B = gridDim.x;
+    const int64_t t0 = tile_lo(nt, blockIdx.x, B), t1 = tile_lo(nt, blockIdx.x + 1, B);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = C.bsum[B + blockIdx.x];
+    __syncthreads();
+    for (int64_t t = t0; t < t1; t++) {
+        const uint32_t* bw = C.bits + t * CTW;
+        const uint32_t mine = bw[warp];
+        if (!((mine >> lane) & 1u)) continue;
+        int before = 0;
+        for (int k = 0; k < warp; k++) before += __popc(bw[k]);
+        const long long pos = base + C.toff[t] + before + __popc(mine & ((1u << lane) - 1u));
+        const int64_t s = t * CT + threadIdx.x;
+        C.tcol[pos] = __ldg(C.col + s);
+        C.teid[pos] = __ldg(C.eid + s);
+    }
+    // new row bounds of every vertex
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < C.n; v += (int64_t)gridDim.x * blockDim.x) {
+        const Off a = C.first ? C.rowptr[v] : C.vstart[v];
+        const Off b = C.first ? C.rowptr[v + 1] : C.vend[v];
+        C.vstart[v] = (Off)live_before(C, (int64_t)a, nt, B);
+        C.vend[v] = (Off)live_before(C, (int64_t)b, nt, B);
+    }
+}
+
+// records of the live edges of `list` (the last Scan's survivors: every
+// unprocessed edge is among them)
+template <typename Off>
+__global__ void k_cmp_records(Compactor<Off> C, const int32_t* __restrict__ list, int64_t k) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = list[i];
+        if (C.ss[e].y < C.g) continue;  // processed
+        const int2 xy = C.el[e];
+        const Off u0 = C.vstart[xy.x], u1 = C.vend[xy.x], v0 = C.vstart[xy.y], v1 = C.vend[xy.y];
+        const bool ushort = u1 - u0 <= v1 - v0;
+        const int32_t lv = ushort ? xy.y : xy.x;
+        const Off llen = ushort ? v1 - v0 : u1 - u0;
+        const int32_t h = C.hub_of ? C.hub_of[lv] : -1;
+        Off* r = C.rows + 4 * (int64_t)e;
+        r[0] = ushort ? u0 : v0;
+        r[1] = ushort ? u1 : v1;
+        if (h >= 0 && llen > 128) {
+            // probed in the hub's bitmap of the row as built
+            r[2] = C.rowptr[lv];
+            r[3] = C.rowptr[lv] + llen;
+            C.lhub[e] = h;
+        } else {
+            r[2] = ushort ? v0 : u0;
+            r[3] = ushort ? v1 : u1;
+            C.lhub[e] = -1;
+        }
+        C.dmin[e] = (int32_t)(ushort ? u1 - u0 : v1 - v0);
+    }
+}
+
+// before a resumed persistent launch: clear the phase slots and the barrier
+// count, keep everything else
+__global__ void k_resume_counters(int* ctr) {
+    for (int i = threadIdx.x; i < C_ERR; i += blockDim.x) ctr[i] = 0;
+    __syncthreads();
+    if (threadIdx.x < 4) clear_slot_vals(slots(ctr) + threadIdx.x);
 }
 
 // --------------------------------------------------------------- helpers
@@ -1128,6 +1290,22 @@ __global__ void k_mark_curr(const int32_t* __restrict__ curr, int64_t k, int2* _
 __global__ void k_inverse_perm(const int32_t* __restrict__ perm, int64_t m, int32_t* __restrict__ inv) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
         inv[perm[e]] = (int32_t)e;
+}
+
+// Validates a caller's frontier before any kernel indexes with it: every id
+// in [0, m) and none twice (seen: a zeroed bitmap of m bits).  Only curr[0,
+// k) and the bitmap are touched; a bad id sets bit 0 of *err, a repeat bit 1.
+__global__ void k_check_curr(const int32_t* __restrict__ curr, int64_t k, int64_t m, uint32_t* __restrict__ seen,
+                             int* __restrict__ err) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = curr[i];
+        if (e < 0 || (int64_t)e >= m) {
+            atomicOr(err, 1);
+            continue;
+        }
+        const uint32_t bit = 1u << (e & 31);
+        if (atomicOr(&seen[e >> 5], bit) & bit) atomicOr(err, 2);
+    }
 }
 
 __global__ void k_map_ids(const int32_t* __restrict__ in, int64_t k, const int32_t* __restrict__ map,
@@ -1243,7 +1421,151 @@ int process_blocks(const truss_graph* g) {
 template <typename Off>
 Graph<Off> graph_view(truss_graph* g) {
     return Graph<Off>{(const Off*)g->rowptr, g->col, g->eid, g->el, g->dmin, (const Off*)g->rows, g->lhub,
-                      g->hub_bits, g->hub_words, g->ss, g->m, g->hc, g->ocap};
+                      g->hub_bits, g->hub_words, g->eid, g->ss, g->m, g->hc, g->ocap};
+}
+
+// ---------------------------------------------------- row compaction (host)
+
+// Compaction of one run: whether it is on, the smallest row set worth
+// compacting, and what it did.
+struct CmpRun {
+    int enabled = 0;
+    int64_t min_held = 0;
+    int buf = -1;             // rows the peel reads: -1 as built, 0 (wcol) or 1 (tcol)
+    int64_t held = 0;         // edges the current rows hold
+    int count = 0;            // compactions run
+    int64_t slots = 0;        // source slots they visited
+};
+
+constexpr int CMP_MAX_BLOCKS = 2048;
+
+int cmp_blocks(const truss_graph* g) { return std::min(CMP_MAX_BLOCKS, std::max(1, g->sms * 4)); }
+
+void truss_release_compaction(truss_graph* g) {
+    cudaFree(g->wcol);
+    cudaFree(g->weid);
+    cudaFree(g->tcol);
+    cudaFree(g->teid);
+    cudaFree(g->wrows);
+    cudaFree(g->wdmin);
+    cudaFree(g->wlhub);
+    cudaFree(g->vstart);
+    cudaFree(g->vend);
+    cudaFree(g->cbits);
+    cudaFree(g->ctoff);
+    cudaFree(g->cbsum);
+    g->wcol = g->weid = g->tcol = g->teid = nullptr;
+    g->wrows = g->vstart = g->vend = nullptr;
+    g->wdmin = g->wlhub = nullptr;
+    g->cbits = nullptr;
+    g->ctoff = nullptr;
+    g->cbsum = nullptr;
+    g->cmp_ready = 0;
+}
+
+// The compaction buffers (about 16 + 4 * sizeof(Off) + 8 bytes per edge, 2
+// Off per vertex).  A graph whose buffers do not fit runs without
+// compaction (TRUSS_ENOMEM is not returned for it).
+int ensure_compaction(truss_graph* g, cudaStream_t s) {
+    if (g->cmp_ready) return TRUSS_OK;
+    const size_t m = (size_t)g->m + 1, osz = g->off64 ? sizeof(int64_t) : sizeof(int32_t);
+    const size_t ntile = (size_t)((2 * g->m + CT - 1) / CT) + 1;
+    bool ok = true;
+    auto get = [&](void** p, size_t bytes) {
+        if (ok && cudaMallocAsync(p, bytes, s) != cudaSuccess) {
+            *p = nullptr;
+            ok = false;
+        }
+    };
+    get((void**)&g->wcol, sizeof(int32_t) * m);
+    get((void**)&g->weid, sizeof(int32_t) * m);
+    get((void**)&g->tcol, sizeof(int32_t) * m);
+    get((void**)&g->teid, sizeof(int32_t) * m);
+    get(&g->wrows, osz * 4 * m);
+    get((void**)&g->wdmin, sizeof(int32_t) * m);
+    get((void**)&g->wlhub, sizeof(int32_t) * m);
+    get(&g->vstart, osz * ((size_t)g->n + 1));
+    get(&g->vend, osz * ((size_t)g->n + 1));
+    get((void**)&g->cbits, sizeof(uint32_t) * CTW * ntile);
+    get((void**)&g->ctoff, sizeof(int32_t) * ntile);
+    get((void**)&g->cbsum, sizeof(long long) * 2 * CMP_MAX_BLOCKS);
+    if (!ok) {
+        cudaGetLastError();  // clear the failed allocation
+        cudaStreamSynchronize(s);
+        truss_release_compaction(g);
+        return TRUSS_ENOMEM;
+    }
+    g->cmp_ready = 1;
+    return TRUSS_OK;
+}
+
+// Compaction settings of a run (TRUSS_LOOP_GRAPH never compacts).
+CmpRun compact_policy(truss_graph* g, const truss_opts& o, cudaStream_t s) {
+    CmpRun c;
+    if (o.loop == TRUSS_LOOP_GRAPH || o.compact == 0 || g->m <= 0) return c;
+    if (o.compact < 0 && g->m < TRUSS_COMPACT_MIN_EDGES) return c;
+    if (ensure_compaction(g, s) != TRUSS_OK) return c;
+    c.enabled = 1;
+    c.min_held = o.compact < 0 ? TRUSS_COMPACT_MIN_EDGES : 0;
+    c.held = g->m;
+    return c;
+}
+
+// The peel's view of compacted rows in buffer `buf` with the working records.
+template <typename Off>
+Graph<Off> view_compacted(truss_graph* g, int buf) {
+    Graph<Off> G = graph_view<Off>(g);
+    G.col = buf == 0 ? g->wcol : g->tcol;
+    G.eid = buf == 0 ? g->weid : g->teid;
+    G.rows = (const Off*)g->wrows;
+    G.dmin = g->wdmin;
+    G.lhub = g->wlhub;
+    return G;
+}
+
+// One compaction before the Scan of a level, at sub-level number gsub, with
+// `list` (k entries) holding every unprocessed edge and `processed` edges
+// peeled so far.  Moves the rows to the other buffer and returns the view.
+template <typename Off>
+int run_compaction(truss_graph* g, CmpRun& c, int32_t gsub, int64_t processed, const int32_t* list, int64_t k,
+                   cudaStream_t s, Graph<Off>* view) {
+    Compactor<Off> C;
+    const int dst = c.buf == 0 ? 1 : 0;
+    C.col = c.buf < 0 ? g->col : (c.buf == 0 ? g->wcol : g->tcol);
+    C.eid = c.buf < 0 ? g->eid : (c.buf == 0 ? g->weid : g->teid);
+    C.nslots = 2 * c.held;
+    C.tcol = dst == 0 ? g->wcol : g->tcol;
+    C.teid = dst == 0 ? g->weid : g->teid;
+    C.vstart = (Off*)g->vstart;
+    C.vend = (Off*)g->vend;
+    C.first = c.buf < 0;
+    C.rowptr = (const Off*)g->rowptr;
+    C.hub_of = g->n_hub > 0 ? g->hub_of : nullptr;
+    C.el = g->el;
+    C.ss = g->ss;
+    C.g = gsub;
+    C.n = g->n;
+    C.rows = (Off*)g->wrows;
+    C.dmin = g->wdmin;
+    C.lhub = g->wlhub;
+    C.bits = g->cbits;
+    C.toff = g->ctoff;
+    C.bsum = g->cbsum;
+    C.live_slots = 2 * (g->m - processed);
+    if (C.live_slots > g->m + 1) return TRUSS_EINVAL;  // the target holds m + 1 slots
+    const int B = cmp_blocks(g);
+    k_cmp_count<Off><<<B, PT, 0, s>>>(C);
+    k_cmp_blocks<<<1, PT, 0, s>>>(g->cbsum, B);
+    k_cmp_scatter<Off><<<B, PT, 0, s>>>(C);
+    if (k > 0) k_cmp_records<Off><<<grid_for(k, 256), 256, 0, s>>>(C, list, k);
+    CU(cudaGetLastError());
+    truss_note_launch(k > 0 ? 4 : 3);
+    c.count++;
+    c.slots += C.nslots;
+    c.buf = dst;
+    c.held = g->m - processed;
+    *view = view_compacted<Off>(g, dst);
+    return TRUSS_OK;
 }
 
 TuneTable tune_table_of(const truss_opts& o) {
@@ -1257,7 +1579,7 @@ Frontier side(truss_graph* g, int k) {
 }
 
 struct RunOut {
-    int64_t nsub = 0, nscan = 0, nlevel = 0, scanned = 0;
+    int64_t nsub = 0, nscan = 0, nlevel = 0, scanned = 0, walked = 0;
     int32_t last_l = 0;
 };
 
@@ -1266,7 +1588,7 @@ struct RunOut {
 // each.  trace (host, may be NULL) receives max_trace sub-level records.
 template <typename Off>
 int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* trace, int64_t max_trace,
-              RunOut* out) {
+              RunOut* out, CmpRun& cmp) {
     Graph<Off> G = graph_view<Off>(g);
     int* ctr = g->ctr;
     int* h = g->h_ctr;
@@ -1293,9 +1615,11 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
     while (processed < g->m && rc == TRUSS_OK) {
         const int32_t* lin = out->nscan == 0 ? nullptr : g->live[(out->nscan + 1) & 1];
         int32_t* lout = g->live[out->nscan & 1];
+        if (cmp.enabled && cmp.held >= cmp.min_held && 2 * (g->m - processed) <= cmp.held && processed > 0)
+            TRY(run_compaction<Off>(g, cmp, gs, processed, lin, nlive, s, &G));
         k_init_counters<<<1, 64, 0, s>>>(ctr);
         if (trace) CU(cudaEventRecord(e0, s));
-        k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, g->dmin, g->hc, g->ocap);
+        k_scan<<<sblocks, PT, 0, s>>>(g->ss, lin, nlive, lout, l, gs, side(g, gs & 1), ctr, G.dmin, g->hc, g->ocap);
         out->scanned += nlive;
         if (trace) CU(cudaEventRecord(e1, s));
         CU(cudaGetLastError());
@@ -1326,6 +1650,7 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
             if (r) *r = truss_sublevel_trace{l, gsz, nl, nh, nc, dmax, dsum, g->m - processed, 0, scan_ns};
             scan_ns = 0;
             processed += nl + nh;
+            out->walked += dsum;
             // the next frontier is counted in slot 1
             k_clear_slot<<<1, 32, 0, s>>>(ctr, 1);
             const int64_t want = std::max<int64_t>(((int64_t)nl * gsz + PT - 1) / PT, ((int64_t)nc * 32 + PT - 1) / PT);
@@ -1378,6 +1703,7 @@ struct GCtl {
     int64_t processed, nsub, nscan, nlevel;
     int64_t nlive;     // entries the next Scan visits
     int64_t scanned;
+    int64_t walked;    // shorter-row entries of all frontiers
     int64_t phases, cap;  // phases run, and the bound on them
     uint64_t t_phase;  // start of the phase that is running
     uint64_t scan_ns;  // Scan time since the last sub-level
@@ -1478,6 +1804,7 @@ __global__ void __launch_bounds__(32) k_gctl(GCtl* c, int* ctr, int64_t m, int v
             }
             s.scan_ns = 0;
             s.processed += (int64_t)s.nl + s.nh;
+            s.walked += s.dsum;
             s.nsub++;
         }
         s.slot ^= 1;
@@ -1488,6 +1815,7 @@ __global__ void __launch_bounds__(32) k_gctl(GCtl* c, int* ctr, int64_t m, int v
             ctr[C_NLEVEL] = (int)s.nlevel;
             ctr[C_LAST_L] = s.l;
             *reinterpret_cast<long long*>(ctr + C_SCANNED) = s.scanned;
+            *reinterpret_cast<long long*>(ctr + C_WALKED) = s.walked;
             if (s.err) ctr[C_ERR] = s.err;
         }
         s.t_phase = global_ns();
@@ -1632,9 +1960,14 @@ inline int persistent_minb(const truss_graph* g, const truss_opts& o, int32_t sm
     return (per_level >= ((int64_t)1 << 24) || g->dmin_sum >= ((int64_t)1 << 34)) ? 6 : 4;
 }
 
+// The persistent loop: one cooperative launch, or, with compaction on, one
+// launch per stretch between compactions -- each launch stops before the
+// Scan of the level whose rows are due, the host compacts them (four
+// launches) and resumes the loop from the state the launch left.  Each stop
+// reads that state back (one synchronisation per compaction).
 template <typename Off, int MINB>
 int launch_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
-                      int64_t max_trace) {
+                      int64_t max_trace, CmpRun& cmp) {
     Graph<Off> G = graph_view<Off>(g);
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<Off, MINB>, PT, 0));
@@ -1653,17 +1986,37 @@ int launch_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss
     int* ctr = g->ctr;
     const float* sched = o.sched_params;
     TuneTable tt = tune_table_of(o);
-    void* args[] = {&G, &f0, &f1, &live0, &live1, &ctr, &variant, &jump, &tmo, &d_trace, &max_trace, &sched, &tt};
-    CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off, MINB>, dim3(blocks), dim3(PT), args, 0, s));
-    truss_note_launch(2);
+    int64_t held = cmp.enabled ? cmp.held : -1;  // -1: the launch never stops early
+    int64_t min_held = cmp.min_held;
+    int resume = 0;
+    for (;;) {
+        void* args[] = {&G,   &f0,        &f1,    &live0, &live1, &ctr,      &variant,  &jump,
+                        &tmo, &d_trace, &max_trace, &sched, &tt,   &held, &min_held, &resume};
+        CU(cudaLaunchCooperativeKernel((const void*)k_persistent<Off, MINB>, dim3(blocks), dim3(PT), args, 0, s));
+        truss_note_launch(resume ? 1 : 2);
+        if (!cmp.enabled) break;
+        int* h = g->h_ctr;
+        CU(cudaMemcpyAsync(h + C_ERR, ctr + C_ERR, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(h + C_ST, ctr + C_ST, sizeof(PState), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        PState ps;
+        memcpy(&ps, h + C_ST, sizeof(ps));
+        if (h[C_ERR] != 0 || !ps.stop) break;
+        const int32_t* lin = (ps.sc & 1) ? live0 : live1;
+        TRY(run_compaction<Off>(g, cmp, ps.g, ps.processed, lin, ps.nlive, s, &G));
+        k_resume_counters<<<1, 64, 0, s>>>(ctr);
+        truss_note_launch();
+        held = cmp.held;
+        resume = 1;
+    }
     return TRUSS_OK;
 }
 
 template <typename Off>
 int run_persistent(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_sublevel_trace* d_trace,
-                   int64_t max_trace, int32_t smax) {
-    if (persistent_minb(g, o, smax) == 4) return launch_persistent<Off, 4>(g, o, s, d_trace, max_trace);
-    return launch_persistent<Off, 6>(g, o, s, d_trace, max_trace);
+                   int64_t max_trace, int32_t smax, CmpRun& cmp) {
+    if (persistent_minb(g, o, smax) == 4) return launch_persistent<Off, 4>(g, o, s, d_trace, max_trace, cmp);
+    return launch_persistent<Off, 6>(g, o, s, d_trace, max_trace, cmp);
 }
 
 int check_opts(const truss_opts& o) {
@@ -1671,8 +2024,14 @@ int check_opts(const truss_opts& o) {
     if (o.variant < TRUSS_VAR_AUTO || o.variant > TRUSS_VAR_LEARNED) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_sub_size) && (!o.h_sub_level || !o.h_sub_size)) return TRUSS_EINVAL;
     if ((o.h_sub_level || o.h_trace) && (o.max_sub < 0 || !o.sync)) return TRUSS_EINVAL;
+    if ((o.h_level_edges || o.h_level_ns) && (o.max_level <= 0 || !o.sync)) return TRUSS_EINVAL;
+    if (o.compact < -1 || o.compact > 1) return TRUSS_EINVAL;
     return TRUSS_OK;
 }
+
+// sub-level records kept for the per-level distribution when the caller
+// asked for no trace of its own
+constexpr int64_t LEVEL_TRACE_CAP = (int64_t)1 << 20;
 
 template <typename Off>
 int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_stats* st, cudaStream_t s) {
@@ -1700,25 +2059,29 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             smax = g->h_ctr[C_TRI + 2];
         }
     }
+    CmpRun cmp = compact_policy(g, o, s);
     if (timed) CU(cudaEventRecord(ev[1], s));
     RunOut ro;
-    const bool rec = (o.h_sub_level || o.h_trace) && o.max_sub > 0;
-    std::vector<truss_sublevel_trace> htr(rec ? (size_t)o.max_sub : 0);
+    const bool lvl = (o.h_level_edges || o.h_level_ns) && o.max_level > 0;
+    const bool rec = ((o.h_sub_level || o.h_trace) && o.max_sub > 0) || lvl;
+    const int64_t tcap = std::max<int64_t>(o.max_sub, lvl ? LEVEL_TRACE_CAP : 0);
+    std::vector<truss_sublevel_trace> htr(rec ? (size_t)tcap : 0);
     int rc = TRUSS_OK;
     if (o.loop == TRUSS_LOOP_PLAIN) {
-        rc = run_plain<Off>(g, o, s, rec ? htr.data() : nullptr, rec ? o.max_sub : 0, &ro);
+        rc = run_plain<Off>(g, o, s, rec ? htr.data() : nullptr, rec ? tcap : 0, &ro, cmp);
     } else {
         truss_sublevel_trace* d_tr = nullptr;
-        if (rec) CU(cudaMallocAsync((void**)&d_tr, sizeof(truss_sublevel_trace) * (size_t)o.max_sub, s));
+        if (rec) CU(cudaMallocAsync((void**)&d_tr, sizeof(truss_sublevel_trace) * (size_t)tcap, s));
         if (o.loop == TRUSS_LOOP_GRAPH)
-            rc = run_graph<Off>(g, o, s, d_tr, rec ? o.max_sub : 0);
+            rc = run_graph<Off>(g, o, s, d_tr, rec ? tcap : 0);
         else
-            rc = run_persistent<Off>(g, o, s, d_tr, rec ? o.max_sub : 0, smax);
+            rc = run_persistent<Off>(g, o, s, d_tr, rec ? tcap : 0, smax, cmp);
         if (rc == TRUSS_OK && o.sync) {
             // the triangle words (C_TRI on) keep the support phase's count on
             // the host side; the peel cleared them on the device
             CU(cudaMemcpyAsync(g->h_ctr, g->ctr, sizeof(int) * C_TRI, cudaMemcpyDeviceToHost, s));
-            CU(cudaMemcpyAsync(g->h_ctr + C_SCANNED, g->ctr + C_SCANNED, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CU(cudaMemcpyAsync(g->h_ctr + C_SCANNED, g->ctr + C_SCANNED, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                               s));
             CU(cudaStreamSynchronize(s));
             if (g->h_ctr[C_ERR]) rc = g->h_ctr[C_ERR];
             ro.nsub = g->h_ctr[C_NSUB];
@@ -1726,11 +2089,12 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
             ro.nlevel = g->h_ctr[C_NLEVEL];
             ro.last_l = g->h_ctr[C_LAST_L];
             memcpy(&ro.scanned, g->h_ctr + C_SCANNED, sizeof(ro.scanned));
+            memcpy(&ro.walked, g->h_ctr + C_WALKED, sizeof(ro.walked));
             // the graph ran a control kernel per phase, a Scan or sub-level
             // kernel in every phase but the last
             if (o.loop == TRUSS_LOOP_GRAPH) truss_note_launch((int)(2 * (ro.nsub + ro.nscan) + 1));
             if (rec && rc == TRUSS_OK) {
-                const int64_t k = std::min<int64_t>(ro.nsub, o.max_sub);
+                const int64_t k = std::min<int64_t>(ro.nsub, tcap);
                 CU(cudaMemcpyAsync(htr.data(), d_tr, sizeof(truss_sublevel_trace) * (size_t)k, cudaMemcpyDeviceToHost, s));
             }
         }
@@ -1763,6 +2127,21 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
                 if (o.h_trace) o.h_trace[i] = htr[i];
             }
         }
+        if (lvl) {
+            // Fig. 6: edges and device time per support level (a level's
+            // time is its sub-levels and the Scans that opened it)
+            for (int32_t i = 0; i < o.max_level; i++) {
+                if (o.h_level_edges) o.h_level_edges[i] = 0;
+                if (o.h_level_ns) o.h_level_ns[i] = 0;
+            }
+            const int64_t k = std::min<int64_t>(ro.nsub, tcap);
+            for (int64_t i = 0; i < k; i++) {
+                const truss_sublevel_trace& r = htr[i];
+                if (r.level < 0 || r.level >= o.max_level) continue;
+                if (o.h_level_edges) o.h_level_edges[r.level] += (int64_t)r.n_light + r.n_heavy;
+                if (o.h_level_ns) o.h_level_ns[r.level] += r.t_ns + r.scan_ns;
+            }
+        }
     }
     if (st) {
         memset(st, 0, sizeof(*st));
@@ -1774,6 +2153,9 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         st->wedges_up = g->wedges_up;
         st->dmin_sum = g->dmin_sum;
         st->scanned = ro.scanned;
+        st->walked = ro.walked;
+        st->compactions = cmp.count;
+        st->compacted_slots = cmp.slots;
         st->grid_blocks = o.loop == TRUSS_LOOP_PLAIN ? 0 : g->last_grid;
         st->blocks_per_sm = o.loop == TRUSS_LOOP_PLAIN ? 0 : g->last_per_sm;
         if (o.sync) {
@@ -1797,8 +2179,27 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
 template <typename Off>
 int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int32_t* d_curr, int64_t ncurr,
                        int32_t l, int32_t* d_next, int64_t* h_nnext, int32_t variant, cudaStream_t s) {
-    TRY(truss_ensure_workspace(g, s));
     const int64_t m = g->m;
+    if (ncurr > 0) {
+        // reject out-of-range or repeated ids before any kernel indexes with them
+        const int64_t words = (m + 31) / 32;
+        uint32_t* seen = nullptr;
+        CU(cudaMallocAsync((void**)&seen, sizeof(uint32_t) * (size_t)words + sizeof(int), s));
+        int* d_err = (int*)(seen + words);
+        CU(cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)words + sizeof(int), s));
+        k_check_curr<<<grid_for(ncurr, 256), 256, 0, s>>>(d_curr, ncurr, m, seen, d_err);
+        int h_err = 0;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(seen, s);
+        if (e != cudaSuccess) {
+            truss_note_cuda_error(e);
+            return TRUSS_ECUDA;
+        }
+        if (h_err) return TRUSS_EBADGRAPH;
+    }
+    TRY(truss_ensure_workspace(g, s));
     int32_t *inv = nullptr, *cur = nullptr;
     CU(cudaMallocAsync((void**)&cur, sizeof(int32_t) * (size_t)(ncurr > 0 ? ncurr : 1), s));
     if (g->perm) {
@@ -1937,6 +2338,7 @@ int truss_ensure_workspace(truss_graph* g, cudaStream_t s) {
 }
 
 void truss_release_workspace(truss_graph* g) {
+    truss_release_compaction(g);
     cudaFree(g->ss);
     cudaFree(g->dmin);
     cudaFree(g->rows);
@@ -2018,6 +2420,72 @@ extern "C" void truss_default_opts(truss_opts* o) {
     o->sync = 0;
     o->level_jump = 1;
     o->timeout_ns = 10000000000ll;
+    o->compact = -1;
+}
+
+// ------------------------------------------- edge-centric support (Alg. 2)
+
+// Ros's support step as Algorithm 2 gives it: every edge {u, v} on its own
+// counts the neighbours of v that are neighbours of u.  Here a warp takes an
+// edge, walks its shorter row (32 entries per round, two per lane) and
+// searches each entry in the longer row -- through the hub bitmap when that
+// row belongs to a hub, else by binary search -- in place of the per-thread
+// marker array X; the count is written once, without atomics.  Warps take
+// edges in batches of ROS_BATCH from a counter, so the few edges with very
+// long rows do not hold up a fixed share of the grid.
+constexpr int ROS_BATCH = 8;
+
+template <typename Off>
+__global__ void __launch_bounds__(PT) k_support_ros(Graph<Off> G, const int32_t* __restrict__ perm,
+                                                    int32_t* __restrict__ out, unsigned long long* next) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(next, (unsigned long long)ROS_BATCH);
+        b0 = __shfl_sync(FULL_MASK, b0, 0);
+        if ((int64_t)b0 >= G.m) break;
+        const int64_t b1 = min((int64_t)b0 + ROS_BATCH, G.m);
+        for (int64_t e = (int64_t)b0; e < b1; e++) {
+            const Rows<Off> r = rows_of<Off>(G, (int32_t)e);
+            int c = 0;
+            for (Off j = r.a0 + lane; j < r.a1; j += 64) {
+                const Off j2 = j + 32;
+                const bool two = j2 < r.a1;
+                const int32_t w1 = __ldg(G.col + j), w2 = two ? __ldg(G.col + j2) : w1;
+                Off q1, q2;
+                if (r.hub >= 0) {
+                    q1 = hub_find<Off>(G, r.hub, r.b0, w1);
+                    q2 = hub_find<Off>(G, r.hub, r.b0, w2);
+                } else {
+                    find2<Off>(G.col, r.b0, r.b1 - r.b0, w1, w2, q1, q2);
+                }
+                c += (q1 >= 0) + (two && q2 >= 0);
+            }
+            c = warp_sum(c);
+            if (lane == 0) out[perm ? perm[e] : e] = c;
+        }
+    }
+}
+
+template <typename Off>
+int support_ros_impl(truss_graph* g, int32_t* d_support, cudaStream_t s) {
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(g->ctr + C_ROS);
+    CU(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_support_ros<Off>, PT, 0));
+    const int blocks = std::max(1, per_sm) * g->sms;
+    k_support_ros<Off><<<blocks, PT, 0, s>>>(graph_view<Off>(g), g->perm, d_support, next);
+    CU(cudaGetLastError());
+    truss_note_launch();
+    return TRUSS_OK;
+}
+
+extern "C" int truss_support_ros(truss_graph* g, int32_t* d_support, void* stream) {
+    if (!g || (g->m > 0 && !d_support)) return TRUSS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(truss_ensure_workspace(g, s));
+    if (g->m == 0) return TRUSS_OK;
+    return g->off64 ? support_ros_impl<int64_t>(g, d_support, s) : support_ros_impl<int32_t>(g, d_support, s);
 }
 
 extern "C" int truss_support(truss_graph* g, int32_t* d_support, void* stream) {

@@ -288,6 +288,34 @@ def test_bad_ids_are_rejected(pkt):
     assert ex.value.status == pkt.EBADGRAPH
 
 
+@pytest.mark.parametrize("relabel", [False, True])
+def test_bad_frontier_ids_are_rejected(pkt, relabel):
+    """A caller's frontier for one ProcessSubLevel is validated on the device
+    before any kernel indexes with it: ids outside [0, m) and repeated ids
+    give EBADGRAPH, more ids than edges EINVAL, and the state is left
+    untouched."""
+    import torch
+
+    # K4: six edges, each in two triangles
+    G = pkt.build_csr(dev([0, 0, 0, 1, 1, 2]), dev([1, 2, 3, 2, 3, 3]), 4, degree_order=relabel)
+    m = G.m
+    for curr, status in (([0, m], pkt.EBADGRAPH), ([-1], pkt.EBADGRAPH), ([2, 2], pkt.EBADGRAPH),
+                         ([0, 1, 2, 3, 4, 5, 0], pkt.EINVAL)):
+        dS = dev([2] * m)
+        flags = torch.zeros(m, dtype=torch.uint8, device="cuda")
+        with pytest.raises(pkt.TrussError) as ex:
+            G.peel_sublevel(dS, flags, dev(curr), 2)
+        assert ex.value.status == status, curr
+        assert host(dS).tolist() == [2] * m and host(flags).tolist() == [0] * m
+    # a valid frontier still runs after the rejections: all six edges at
+    # level 2 are processed together, and no support changes
+    dS = dev([2] * m)
+    flags = torch.zeros(m, dtype=torch.uint8, device="cuda")
+    nxt = G.peel_sublevel(dS, flags, dev(list(range(m))), 2)
+    assert nxt.numel() == 0 and host(dS).tolist() == [2] * m
+    assert host(flags).tolist() == [pkt.PROCESSED] * m
+
+
 @pytest.mark.parametrize("loop", ["persistent_lat", "persistent_occ", "graph"])
 def test_barrier_wait_limit_returns_status(pkt, loop):
     """A grid-barrier wait (persistent forms) or a phase (graph form) that
@@ -536,3 +564,27 @@ def test_triangle_count(pkt):
     _, st = G.decompose(stats=True)
     assert G.triangle_count() == st["triangles"]
     G.free()
+
+
+@pytest.mark.parametrize("relabel,off64", [(True, False), (False, False), (True, True)])
+def test_edge_centric_support_matches_oracle(pkt, relabel, off64):
+    """Algorithm 2's edge-centric support (every edge counts its common
+    neighbours on its own) equals the oracle's S(e) element by element, on
+    graphs with short rows, hub rows (bitmap probes), a wheel whose hub row
+    spans many rounds of a warp, and the empty graph."""
+    k = 3000
+    wheel = gg.EdgeList(k + 1, np.concatenate([np.zeros(k), np.arange(1, k + 1)]).astype(np.int32),
+                        np.concatenate([np.arange(1, k + 1), np.arange(1, k + 1) % k + 1]).astype(np.int32), "wheel")
+    hubs = gg.chung_lu(20000, 2.1, 20.0, 5000.0, seed=13)
+    for name, g in SMALL + [("wheel", wheel), ("hubs", hubs)]:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, **_flags(relabel, off64))
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        want = oracle.support(g.n, eu, ev)
+        assert np.array_equal(host(G.support_ros()), want), name
+        # unchanged by a decomposition (and its compactions) before it
+        G.decompose(compact=1)
+        assert np.array_equal(host(G.support_ros()), want), name
+        G.free()
+    e = dev(np.zeros(0, np.int32))
+    G = pkt.build_csr(e, e, 4)
+    assert G.support_ros().numel() == 0
