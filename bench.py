@@ -151,7 +151,10 @@ class ClockSampler:
 
 def algorithmic_bytes(st, n):
     """Compulsory bytes of each phase, from exact work counts reported by the
-    library: support = 32m + 8n + 4W+ + 12T; peeling = (16 V - 8m) for the
+    library: support = 32m + 8n + 4 Wv + 32 Wh + 12T, where Wv = the N+(v)
+    entries the support kernels read (W+ = sum_v d-(v) d+(v) when no pair
+    switches to a hub bitmap) and Wh = the hub-bitmap probes (one 32-byte
+    block each); peeling = (16 V - 8m) for the
     Scans (V = entries visited: an 8-byte support/stamp read per entry, plus
     a 4-byte id read and a 4-byte survivor write after the first Scan) +
     36m + 4 X + 28T + 24 C, where X = the shorter-row entries walked (the
@@ -160,7 +163,8 @@ def algorithmic_bytes(st, n):
     entries the compactions visited (4-byte neighbour, 4-byte id and 8-byte
     support/stamp read, 8 bytes written per entry at most)."""
     m, T = st["m"], st["triangles"]
-    sup = 32 * m + 8 * n + 4 * st["wedges_up"] + 12 * T
+    wv = st.get("support_walked") or st["wedges_up"]
+    sup = 32 * m + 8 * n + 4 * wv + 32 * st.get("support_hub_probes", 0) + 12 * T
     walked = st.get("walked", st["dmin_sum"])
     peel = (16 * st["scanned"] - 8 * m) + 36 * m + 4 * walked + 28 * T + 24 * st.get("compacted_slots", 0)
     return sup, peel
@@ -260,12 +264,10 @@ VARIANT_DESC = {"learned": "learned cost model per sub-level (heuristic below 64
 
 
 def calibration_graphs(gg):
-    """Other members of the workloads' families (seed 101), the scheduler's
-    training graphs; the R-MAT family enters at scale 21."""
-    return [("rmat10_ef8 seed 101", gg.workload("rmat10_ef8", 101)),
-            ("chunglu_n2^20_d20 seed 101", gg.workload("chunglu_n2^20_d20", 101)),
-            ("rgg2d_n2^21_d32 seed 101", gg.workload("rgg2d_n2^21_d32", 101)),
-            ("R-MAT scale 21 edge factor 16 seed 101", gg.rmat(21, 16, seed=101))]
+    """Other members of the workloads' families at the workloads' sizes
+    (seed 101), the scheduler's training graphs (yielded one at a time)."""
+    for name in ("rmat10_ef8", "chunglu_n2^20_d20", "rgg2d_n2^21_d32", "rmat24_ef16"):
+        yield f"{name} seed 101", gg.workload(name, 101), name in OFFSETS64
 
 
 def calibrate(pkt, repeats=2, epochs=2000):
@@ -279,10 +281,12 @@ def calibrate(pkt, repeats=2, epochs=2000):
 
     t0 = time.perf_counter()
     xs, ys, names = [], [], []
-    for name, c in calibration_graphs(gg):
-        Gc = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n)
+    for name, c, off64 in calibration_graphs(gg):
+        Gc = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n, offsets64=off64)
+        del c
         x, y = pkt.sched_dataset(Gc, repeats=repeats)
         Gc.free()
+        torch.cuda.empty_cache()
         xs.append(x)
         ys.append(y)
         names.append(name)
@@ -384,6 +388,33 @@ def run_gpu(args):
                 stats.append(st)
         return per, stats
 
+    def device_ms(fn, steps):
+        """Mean CUDA-event time of fn() over `steps` calls after one warm-up,
+        L2 flushed before each."""
+        fn()
+        barrier()
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.mean(out), r
+
+    def contrast_forms(Gc, oc, steps):
+        """The paper's comparison points on the same graph: Algorithm 2's
+        edge-centric support (Ros) beside the oriented support the step uses,
+        and the asynchronous local h-index iteration beside the peel."""
+        ms_ros, _ = device_ms(lambda: Gc.support_ros(out=oc), steps)
+        ms_sup, _ = device_ms(lambda: Gc.support(out=oc), steps)
+        ms_loc, st = device_ms(lambda: Gc.decompose_local(out=oc, stats=True)[1], steps)
+        return {"support_ms": ms_sup, "support_ros_ms": ms_ros, "local_ms": ms_loc,
+                "local_sweeps": st["sweeps"], "local_updates": st["updates"]}
+
     def config_entry(name, n, m, results):
         rec = {"workload": WORKLOAD_DESC.get(name, name), "n": n, "m": m,
                "forms": {k: form_record(*v) for k, v in results.items()}}
@@ -418,7 +449,8 @@ def run_gpu(args):
                      "replicas": ws, "triangles": st0["triangles"], "t_max": st0["t_max"],
                      "sublevels": st0["sublevels"], "scans": st0["scans"], "scanned_entries": st0["scanned"],
                      "dmin_sum": st0["dmin_sum"], "walked": st0["walked"], "compactions": st0["compactions"],
-                     "compacted_slots": st0["compacted_slots"], "wedges_up": st0["wedges_up"]}
+                     "compacted_slots": st0["compacted_slots"], "wedges_up": st0["wedges_up"],
+                     "support_walked": st0["support_walked"], "support_hub_probes": st0["support_hub_probes"]}
     if calib is not None:
         res["config"]["scheduler_calibration"] = calib
     # the paper's own rate: wedges |^| = sum_v d(v)(d(v)-1)/2 per second
@@ -507,6 +539,7 @@ def run_gpu(args):
             oc = torch.empty(max(Gc.m, 1), dtype=torch.int32, device="cuda")
             results = {f: timed(Gc, oc, lf, vf, ks, kw, params) for f, (lf, vf) in forms.items()}
             configs[name] = config_entry(name, c.n, Gc.m, results)
+            configs[name]["contrast"] = contrast_forms(Gc, oc, ks)
             Gc.free()
             del oc, c
     if configs:

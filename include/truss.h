@@ -247,7 +247,8 @@ typedef struct truss_opts {
     int32_t compact;      /* row compaction between levels (persistent and
                              plain loops): -1 automatic (graphs of at least
                              TRUSS_COMPACT_MIN_EDGES edges), 0 off, 1 on for
-                             any size.  Once at most half of the edges the
+                             any size.  Once at most 50 % (80 % while the
+                             rows hold 2^25 edges or more) of the edges the
                              rows hold are unprocessed, the entries of
                              processed edges are dropped from the rows, so
                              ProcessSubLevel walks and searches only live
@@ -292,6 +293,12 @@ typedef struct truss_stats {
                             lengths as the rows stood then (dmin_sum without
                             compaction; sync = 1)                           */
     int64_t compacted_slots; /* row entries the compactions visited (sync)  */
+    int64_t support_walked;  /* N+(v) entries the support kernels read (at
+                            most wedges_up: a pair u < v whose v is a hub
+                            with a bitmap and whose N+(v) is longer than
+                            u's entries above v walks those entries instead,
+                            probing v's bitmap; sync = 1)                   */
+    int64_t support_hub_probes; /* those bitmap probes (sync = 1)          */
 } truss_stats;
 
 /*

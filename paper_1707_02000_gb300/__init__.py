@@ -73,7 +73,8 @@ class Stats(ctypes.Structure):
                 ("wedges_up", ctypes.c_int64), ("dmin_sum", ctypes.c_int64), ("scanned", ctypes.c_int64),
                 ("grid_blocks", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("max_support", ctypes.c_int32), ("compactions", ctypes.c_int32), ("walked", ctypes.c_int64),
-                ("compacted_slots", ctypes.c_int64)]
+                ("compacted_slots", ctypes.c_int64), ("support_walked", ctypes.c_int64),
+                ("support_hub_probes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

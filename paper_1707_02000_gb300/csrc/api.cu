@@ -7,7 +7,7 @@
 
 // The Python binding mirrors these layouts.
 static_assert(sizeof(truss_opts) == 104, "truss_opts layout");
-static_assert(sizeof(truss_stats) == 112, "truss_stats layout");
+static_assert(sizeof(truss_stats) == 128, "truss_stats layout");
 static_assert(sizeof(truss_sublevel_trace) == 56, "truss_sublevel_trace layout");
 
 extern "C" int truss_decompose_host(const int32_t* h_src, const int32_t* h_dst, int64_t n_in, int32_t n,

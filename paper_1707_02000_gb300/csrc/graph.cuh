@@ -34,12 +34,14 @@
 //                     neighbours before the block, 3 x 64 neighbour bits}
 //   ctr    int[...]   device counters (see peel.cu)
 // Row compaction (peel.cu; allocated on the first decomposition that uses it):
-//   wcol, weid int32[2m]  working copy of the rows; between levels the
+//   wcol, weid int32[.]   rows after a compaction; between levels the
 //                     entries of processed edges are dropped from it, so the
 //                     rows the peel walks and searches shrink as it goes
-//   tcol, teid int32[m]   scatter target of a compaction (a compaction runs
-//                     once at most half of the held edges are live, so the
-//                     live entries fit in m slots)
+//   tcol, teid int32[.]   scatter target of a compaction (a compaction runs
+//                     once at most 80 % (2^25 edges held or more) or 50 % of
+//                     the held edges are live, so the live entries of the
+//                     first one fit in 1.6 m or m slots; both buffers take
+//                     that many)
 //   wrows, wdmin, wlhub   working copies of rows / dmin / lhub, rewritten
 //                     for the live edges by each compaction
 //   vstart, vend Off[n]  current row bounds of every vertex in wcol
@@ -48,6 +50,10 @@
 #include "common.cuh"
 
 #define TRUSS_STAMP_NONE 0x7fffffff
+
+// Words of the counter block (int index) where the support kernels count
+// their work: u64 N+(v) entries walked, u64 hub-bitmap probes.
+#define TRUSS_CTR_SUPPORT_WORK 50
 
 // Support-kernel classes by upper degree d+(u): the warp-per-vertex kernel
 // takes d+(u) <= TRUSS_SUP_WARP_CAP (its 128-entry instance when no d+(u)
@@ -87,6 +93,8 @@ struct truss_graph {
     int64_t max_updeg = 0;
     int64_t wedges_up = 0;  // sum_v d-(v) d+(v)
     int64_t dmin_sum = 0;   // sum_e min(d(u), d(v))
+    int sup_switch = 0;     // support kernels switch sides at hubs (truss_support_plan)
+    int64_t sup_gain = 0;   // N+(v) entries the switch saves
     int hc = 64;            // heavy-edge chunk length used by ProcessSubLevel
     // peeling workspace
     int2* ss = nullptr;
@@ -110,8 +118,10 @@ struct truss_graph {
     int latched = 0;       // latched device-side error status
 };
 
-// Implemented in support.cu: fills ss[e].x = S(e) for every internal edge.
+// Implemented in support.cu: fills ss[e].x = S(e) for every internal edge;
+// truss_support_plan decides the hub side switch once the bitmaps exist.
 int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s);
+int truss_support_plan(truss_graph* g, cudaStream_t s);
 // Implemented in peel.cu.
 int truss_ensure_workspace(truss_graph* g, cudaStream_t s);
 void truss_release_workspace(truss_graph* g);

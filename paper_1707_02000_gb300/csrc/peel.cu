@@ -64,6 +64,7 @@ enum {
     C_SCANNED = 44,  // [44..45] entries all Scans visited (i64)
     C_WALKED = 46,   // [46..47] shorter-row entries of all frontiers (i64)
     C_ROS = 48,      // [48..49] next edge batch of the edge-centric support (u64)
+    // [50..53] the support kernels' work counters (TRUSS_CTR_SUPPORT_WORK)
     C_ST = 64,       // [64..95] loop state a persistent launch leaves (PState)
     C_TOTAL = 96
 };
@@ -76,6 +77,16 @@ struct PState {
     long long processed, nsub, sc, nlevel, nlive, scanned, walked, scan_ns;
 };
 static_assert(sizeof(PState) <= sizeof(int) * (C_TOTAL - C_ST), "PState fits the counter block");
+
+// A compaction runs once the live (unprocessed) edges are at most this
+// share (in %) of the edges the rows hold: 80 % while the rows hold at
+// least 2^25 edges (the walk saved outweighs the passes), 50 % below (each
+// compaction also costs a stop of the persistent launch and a host round
+// trip).  Measured: R-MAT scale 24 peel 1.51 s at 50 %, 1.32 s at 65 %,
+// 1.21 s at 80 %, 1.22 s at 90 %; Chung-Lu 2^20 and the geometric 2^21
+// graph are fastest at 50 % (80 %: +3 % and +7 %).
+constexpr int64_t CMP_BIG_HELD = (int64_t)1 << 25;
+__host__ __device__ __forceinline__ int cmp_live_pct(int64_t held) { return held >= CMP_BIG_HELD ? 80 : 50; }
 
 constexpr int PT = 256;      // threads per block in the peel kernels
 constexpr int PW = PT / 32;
@@ -808,13 +819,18 @@ __global__ void k_classify(const int32_t* __restrict__ edges, int64_t k, const i
 
 // one sub-level: lists of side `cur` with the counts given, next lists into
 // side `nxt` counted in slot 1
+// In a decomposition run (in_run) level 0 is the first level, so its edges
+// have had support 0 from the start: they lie in no triangle and there is
+// nothing to walk.  A caller-set state (truss_peel_sublevel) may differ.
+__device__ __forceinline__ bool walk_needed(int32_t l, int in_run) { return l > 0 || !in_run; }
+
 template <typename Off>
 __global__ void __launch_bounds__(PT) k_process(Graph<Off> G, Frontier cur, int nl, int nh, uint32_t nchunk, int gsz,
-                                                int32_t l, int32_t g, Frontier nxt, int* ctr) {
+                                                int32_t l, int32_t g, Frontier nxt, int* ctr, int in_run) {
     __shared__ PeelSmem sm;
     smem_init(&sm);
     const Appender ap{&sm, nxt, slot_of(ctr, 1), G.dmin, G.hc, G.ocap};
-    process_frontier<Off>(G, cur, nl, nh, nchunk, gsz, l, g, ap);
+    if (walk_needed(l, in_run)) process_frontier<Off>(G, cur, nl, nh, nchunk, gsz, l, g, ap);
     ap.flush();
 }
 
@@ -884,9 +900,9 @@ __device__ bool grid_barrier(int* ctr, unsigned nblocks, uint64_t timeout_ns, un
 // dependent-load chains of many small sub-levels of long rows fastest.
 // Measured on the power-law and geometric workloads against 5 and 7.
 // With `held` >= 0 the launch also stops (stop = 1) at the top of a level
-// once at most half of the `held` edges its rows hold are unprocessed (and
-// held >= min_held): the host then compacts the rows and resumes the loop
-// with `resume` set, from the state in the counter block.
+// once at most cmp_live_pct(held) % of the `held` edges its rows hold are
+// unprocessed (and held >= min_held): the host then compacts the rows and
+// resumes the loop with `resume` set, from the state in the counter block.
 template <typename Off, int MINB>
 __global__ void __launch_bounds__(PT, MINB)
     k_persistent(Graph<Off> G, Frontier f0, Frontier f1, int32_t* live0, int32_t* live1, int* ctr, int variant,
@@ -919,7 +935,7 @@ __global__ void __launch_bounds__(PT, MINB)
     }
     int stop = 0;
     while (processed < G.m) {
-        if (held >= min_held && 2 * (G.m - processed) <= held && processed > 0) {
+        if (held >= min_held && (G.m - processed) * 100 <= held * cmp_live_pct(held) && processed > 0) {
             stop = 1;  // the rows are due for compaction
             break;
         }
@@ -983,11 +999,11 @@ __global__ void __launch_bounds__(PT, MINB)
                 t0 = global_ns();
             }
             processed += nl + nh;
-            walked += (int64_t)v.dsum;
+            if (l > 0) walked += (int64_t)v.dsum;
             const Frontier cu = (g & 1) ? f1 : f0;
             const Frontier nx = (g & 1) ? f0 : f1;
             const Appender ap{&sm, nx, slot_of(ctr, q), G.dmin, G.hc, G.ocap};
-            process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
+            if (walk_needed(l, 1)) process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
             ap.flush();
             if (!grid_barrier(ctr, nblocks, timeout_ns, epoch, q, &sv)) return;
             if (leader && nsub < max_trace) trace[nsub].t_ns = (int64_t)(global_ns() - t0);
@@ -1023,8 +1039,8 @@ __global__ void __launch_bounds__(PT, MINB)
 //
 // A processed edge never takes part in a triangle again (Algorithm 5 skips
 // every triangle with a processed edge), so its two row entries can leave
-// the rows.  Between levels, once at most half of the edges the rows hold
-// are unprocessed, the live entries are packed into a second buffer (rows
+// the rows.  Between levels, once few enough of the edges the rows hold are
+// unprocessed (cmp_live_pct), the live entries are packed into a second buffer (rows
 // keep their order and follow one another), every vertex gets its new row
 // bounds, and every live edge new records: its shorter live row (walked),
 // its longer live row (searched) and the walk length dmin, which also sets
@@ -1069,6 +1085,7 @@ struct Compactor {
     int32_t* toff;       // per tile: live slots before it within its block's range
     long long* bsum;     // per block: live total [0, B), then its offset [B, 2B)
     int64_t live_slots;  // 2 x unprocessed edges: slots in the target
+    int64_t hub_min;     // a hub's longer row is probed in its bitmap above this many live entries
 };
 
 // block b of B takes tiles [nt b / B, nt (b + 1) / B)
@@ -1197,7 +1214,7 @@ __global__ void k_cmp_records(Compactor<Off> C, const int32_t* __restrict__ list
         Off* r = C.rows + 4 * (int64_t)e;
         r[0] = ushort ? u0 : v0;
         r[1] = ushort ? u1 : v1;
-        if (h >= 0 && llen > 128) {
+        if (h >= 0 && llen > (Off)C.hub_min) {
             // probed in the hub's bitmap of the row as built
             r[2] = C.rowptr[lv];
             r[3] = C.rowptr[lv] + llen;
@@ -1426,6 +1443,7 @@ Graph<Off> graph_view(truss_graph* g) {
 
 // ---------------------------------------------------- row compaction (host)
 
+
 // Compaction of one run: whether it is on, the smallest row set worth
 // compacting, and what it did.
 struct CmpRun {
@@ -1438,8 +1456,19 @@ struct CmpRun {
 };
 
 constexpr int CMP_MAX_BLOCKS = 2048;
+// After a compaction a hub's longer row is probed in its bitmap only while
+// it holds more than this many live entries; shorter rows are searched (128
+// entries and fewer fit the register-resident warp search).  Measured on
+// R-MAT scale 24: peel 1.22 s at 128 and 1024, 1.32 s at 8192, 1.43 s with
+// no bitmap after the first compaction (Chung-Lu 2^20: 32.9 / 35.8 / 37.7 /
+// 37.8 ms): the bitmaps keep paying on compacted rows.
+constexpr int64_t CMP_HUB_MIN_LIVE = 128;
 
 int cmp_blocks(const truss_graph* g) { return std::min(CMP_MAX_BLOCKS, std::max(1, g->sms * 4)); }
+
+// Slots each row buffer holds: the live entries of the first compaction,
+// at most 2 m cmp_live_pct(m) / 100 (later ones hold fewer).
+size_t cmp_slots(const truss_graph* g) { return (size_t)(2 * g->m * cmp_live_pct(g->m) / 100) + 1; }
 
 void truss_release_compaction(truss_graph* g) {
     cudaFree(g->wcol);
@@ -1469,6 +1498,7 @@ void truss_release_compaction(truss_graph* g) {
 int ensure_compaction(truss_graph* g, cudaStream_t s) {
     if (g->cmp_ready) return TRUSS_OK;
     const size_t m = (size_t)g->m + 1, osz = g->off64 ? sizeof(int64_t) : sizeof(int32_t);
+    const size_t slots = cmp_slots(g);
     const size_t ntile = (size_t)((2 * g->m + CT - 1) / CT) + 1;
     bool ok = true;
     auto get = [&](void** p, size_t bytes) {
@@ -1477,10 +1507,10 @@ int ensure_compaction(truss_graph* g, cudaStream_t s) {
             ok = false;
         }
     };
-    get((void**)&g->wcol, sizeof(int32_t) * m);
-    get((void**)&g->weid, sizeof(int32_t) * m);
-    get((void**)&g->tcol, sizeof(int32_t) * m);
-    get((void**)&g->teid, sizeof(int32_t) * m);
+    get((void**)&g->wcol, sizeof(int32_t) * slots);
+    get((void**)&g->weid, sizeof(int32_t) * slots);
+    get((void**)&g->tcol, sizeof(int32_t) * slots);
+    get((void**)&g->teid, sizeof(int32_t) * slots);
     get(&g->wrows, osz * 4 * m);
     get((void**)&g->wdmin, sizeof(int32_t) * m);
     get((void**)&g->wlhub, sizeof(int32_t) * m);
@@ -1552,7 +1582,8 @@ int run_compaction(truss_graph* g, CmpRun& c, int32_t gsub, int64_t processed, c
     C.toff = g->ctoff;
     C.bsum = g->cbsum;
     C.live_slots = 2 * (g->m - processed);
-    if (C.live_slots > g->m + 1) return TRUSS_EINVAL;  // the target holds m + 1 slots
+    C.hub_min = CMP_HUB_MIN_LIVE;
+    if ((size_t)C.live_slots > cmp_slots(g)) return TRUSS_EINVAL;  // beyond the target's capacity
     const int B = cmp_blocks(g);
     k_cmp_count<Off><<<B, PT, 0, s>>>(C);
     k_cmp_blocks<<<1, PT, 0, s>>>(g->cbsum, B);
@@ -1615,7 +1646,8 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
     while (processed < g->m && rc == TRUSS_OK) {
         const int32_t* lin = out->nscan == 0 ? nullptr : g->live[(out->nscan + 1) & 1];
         int32_t* lout = g->live[out->nscan & 1];
-        if (cmp.enabled && cmp.held >= cmp.min_held && 2 * (g->m - processed) <= cmp.held && processed > 0)
+        if (cmp.enabled && cmp.held >= cmp.min_held && (g->m - processed) * 100 <= cmp.held * cmp_live_pct(cmp.held) &&
+            processed > 0)
             TRY(run_compaction<Off>(g, cmp, gs, processed, lin, nlive, s, &G));
         k_init_counters<<<1, 64, 0, s>>>(ctr);
         if (trace) CU(cudaEventRecord(e0, s));
@@ -1650,13 +1682,14 @@ int run_plain(truss_graph* g, const truss_opts& o, cudaStream_t s, truss_subleve
             if (r) *r = truss_sublevel_trace{l, gsz, nl, nh, nc, dmax, dsum, g->m - processed, 0, scan_ns};
             scan_ns = 0;
             processed += nl + nh;
-            out->walked += dsum;
+            if (l > 0) out->walked += dsum;
             // the next frontier is counted in slot 1
             k_clear_slot<<<1, 32, 0, s>>>(ctr, 1);
             const int64_t want = std::max<int64_t>(((int64_t)nl * gsz + PT - 1) / PT, ((int64_t)nc * 32 + PT - 1) / PT);
             const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(pmax, want));
             if (r) CU(cudaEventRecord(e0, s));
-            k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, gs & 1), nl, nh, nc, gsz, l, gs, side(g, (gs + 1) & 1), ctr);
+            k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, gs & 1), nl, nh, nc, gsz, l, gs, side(g, (gs + 1) & 1), ctr,
+                                                 1);
             if (r) CU(cudaEventRecord(e1, s));
             CU(cudaGetLastError());
             truss_note_launch(2);
@@ -1804,7 +1837,7 @@ __global__ void __launch_bounds__(32) k_gctl(GCtl* c, int* ctr, int64_t m, int v
             }
             s.scan_ns = 0;
             s.processed += (int64_t)s.nl + s.nh;
-            s.walked += s.dsum;
+            if (s.l > 0) s.walked += s.dsum;
             s.nsub++;
         }
         s.slot ^= 1;
@@ -1847,7 +1880,7 @@ __global__ void __launch_bounds__(PT) k_gprocess(Graph<Off> G, const GCtl* c, Fr
     const int32_t l = c->l, g = c->g;
     const Frontier cu = (g & 1) ? f1 : f0, nx = (g & 1) ? f0 : f1;
     const Appender ap{&sm, nx, slot_of(ctr, slot), G.dmin, G.hc, G.ocap};
-    process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
+    if (walk_needed(l, 1)) process_frontier<Off>(G, cu, nl, nh, nchunk, gsz, l, g, ap);
     ap.flush();
 }
 
@@ -2054,6 +2087,8 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         CU(cudaGetLastError());
         truss_note_launch();
         CU(cudaMemcpyAsync(g->h_ctr + C_TRI, g->ctr + C_TRI, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(g->h_ctr + TRUSS_CTR_SUPPORT_WORK, g->ctr + TRUSS_CTR_SUPPORT_WORK,
+                           2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         if (pick) {
             CU(cudaStreamSynchronize(s));
             smax = g->h_ctr[C_TRI + 2];
@@ -2154,6 +2189,14 @@ int decompose_impl(truss_graph* g, int32_t* d_truss, const truss_opts& o, truss_
         st->dmin_sum = g->dmin_sum;
         st->scanned = ro.scanned;
         st->walked = ro.walked;
+        if (o.sync && g->sup_switch) {
+            unsigned long long sw[2];
+            memcpy(sw, g->h_ctr + TRUSS_CTR_SUPPORT_WORK, sizeof(sw));
+            st->support_walked = (int64_t)sw[0];
+            st->support_hub_probes = (int64_t)sw[1];
+        } else {
+            st->support_walked = g->wedges_up;  // no side switch: the walk is exactly W+
+        }
         st->compactions = cmp.count;
         st->compacted_slots = cmp.slots;
         st->grid_blocks = o.loop == TRUSS_LOOP_PLAIN ? 0 : g->last_grid;
@@ -2225,7 +2268,7 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
         Graph<Off> G = graph_view<Off>(g);
         const int blocks = process_blocks<Off>(g);
         k_process<Off><<<blocks, PT, 0, s>>>(G, side(g, 0), nl, nh, nc, pick_group(variant, nl, 0, nl + nh, tune_table_of(truss_opts{})), l,
-                                             1, side(g, 1), g->ctr);
+                                             1, side(g, 1), g->ctr, 0);
         CU(cudaGetLastError());
     }
     CU(cudaMemcpyAsync(h, g->ctr, sizeof(int) * C_BAR_COUNT, cudaMemcpyDeviceToHost, s));
@@ -2321,6 +2364,7 @@ int truss_ensure_workspace(truss_graph* g, cudaStream_t s) {
     CU(cudaMallocAsync((void**)&g->lhub, sizeof(int32_t) * m, s));
     if (g->m > 0) {
         TRY(g->off64 ? build_hubs<int64_t>(g, s) : build_hubs<int32_t>(g, s));
+        TRY(truss_support_plan(g, s));
         if (g->off64)
             k_dmin<int64_t><<<grid_for(g->m, 256), 256, 0, s>>>((const int64_t*)g->rowptr, g->el, g->m, g->dmin,
                                                                  (int64_t*)g->rows, g->hub_of, g->lhub);
@@ -2349,6 +2393,7 @@ void truss_release_workspace(truss_graph* g) {
     g->lhub = g->hub_of = nullptr;
     g->hub_bits = nullptr;
     g->n_hub = 0;
+    g->sup_switch = 0;
     for (int k = 0; k < 2; k++) {
         for (int j = 0; j < 3; j++) {
             cudaFree(g->fq[k][j]);

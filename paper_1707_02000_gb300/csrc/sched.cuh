@@ -32,11 +32,20 @@ __host__ __device__ __forceinline__ void sched_features(int64_t size, int64_t ds
     x[4] = log2f(1.f + (float)todo);
 }
 
+// A sub-level whose normalised features lie further than this many standard
+// deviations from the training mean is outside what the model was fitted
+// on: the fixed heuristic decides it.
+constexpr float SCHED_Z_MAX = 4.f;
+
 // Warp-cooperative inference (all 32 lanes call): lane j computes hidden unit
 // j of each layer; returns the variant with the smallest predicted time, or
-// -1 when the model yields a non-finite value.
+// -1 (the heuristic decides) when a feature is out of the training range or
+// the model yields a non-finite value.
 __device__ __forceinline__ int sched_pick(const float* __restrict__ p, const float* x) {
     const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < SF; i++)
+        if (fabsf((x[i] - __ldg(p + SP_MU + i)) * __ldg(p + SP_ISD + i)) > SCHED_Z_MAX) return -1;
     float a = __ldg(p + SP_B1 + lane);
 #pragma unroll
     for (int i = 0; i < SF; i++) a = fmaf(__ldg(p + SP_W1 + lane * SF + i), (x[i] - __ldg(p + SP_MU + i)) * __ldg(p + SP_ISD + i), a);

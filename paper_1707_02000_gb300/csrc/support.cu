@@ -34,6 +34,14 @@ namespace {
 
 constexpr int SW_WARPS = 8;  // warps per block, warp-per-vertex kernel
 constexpr int SW_SPLIT = TRUSS_SUP_SPLIT;  // rows up to here go to the smaller instance
+// Switch sides at a hub v when N+(v) is longer than SUP_SWITCH_FACTOR times
+// u's entries above v (R-MAT scale 24 support: 1.07 s at 1, 1.08 at 2, 1.10
+// at 4, 1.15 at 8; Chung-Lu 2^20: 3.65 / 3.89 / 4.08 / 4.33 ms).
+constexpr int SUP_SWITCH_FACTOR = 1;
+// The switching instances hold more registers (fewer warps an SM), so a
+// graph uses them only when the switch saves at least 1/SUP_SWITCH_MIN_GAIN
+// of W+ (the 4096-graph batch saves 0.3 % and runs 40 % slower with them).
+constexpr int SUP_SWITCH_MIN_GAIN = 10;
 
 // S accumulates in a plain int32[m] array (half the footprint of the
 // {S, stamp} pairs, so more of the random per-triangle atomics hit L2); the
@@ -59,14 +67,51 @@ __device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, in
     return lo;
 }
 
+// The peel's hub bitmaps (full rows of the highest-degree vertices, 32-byte
+// blocks of 192 vertex ids led by the count of neighbours before the block),
+// used by the support kernels to switch sides; hub_of == nullptr: no hubs.
+struct HubView {
+    const int32_t* hub_of;
+    const unsigned long long* bits;
+    int64_t hw;
+    int factor;  // switch when N+(v) is longer than factor x u's entries above v
+};
+
+// Rank of w among the neighbours of the hub h's vertex, or -1 when w is not
+// one of them (one 32-byte block read).
+__device__ __forceinline__ int64_t hub_rank(const HubView& hv, int32_t h, int32_t w) {
+    const int32_t b = w / 192, r = w - b * 192;
+    const ulonglong2* B = reinterpret_cast<const ulonglong2*>(hv.bits + (int64_t)h * hv.hw + 4 * (int64_t)b);
+    const ulonglong2 lo = __ldg(B), hi = __ldg(B + 1);
+    const int k = r >> 6, bit = r & 63;
+    const unsigned long long word = k == 0 ? lo.y : (k == 1 ? hi.x : hi.y);
+    if (!((word >> bit) & 1ull)) return -1;
+    int64_t rank = (int64_t)(uint32_t)lo.x;
+    if (k > 0) rank += __popcll(lo.y);
+    if (k > 1) rank += __popcll(hi.x);
+    return rank + __popcll(word & ((1ull << bit) - 1ull));
+}
+
 // Vertices u with d+(u) <= CAP (longer rows go to the block kernels).  With
 // COUNT the kernels only count triangles into *tri (no edge ids, no
 // per-edge atomics).
-template <typename Off, int CAP, bool COUNT = false>
+//
+// Switching sides at hubs: for a pair u < v (v in N+(u), at position p),
+// the triangles u < v < w are the w in N+(v) that are also in N+(u) above
+// position p.  When v is a hub and N+(v) is longer than those d - 1 - p
+// entries, the kernel walks the entries instead (they are staged) and asks
+// v's bitmap about each -- one block read -- so the pair costs
+// min(d+(v), d - 1 - p) probes instead of d+(v).  Such pairs are marked by a
+// negative E[p] = -(hub index + 1) and get length 0 in the N+(v) walk.
+// HUB: the instance that switches sides at hubs (graphs with hub bitmaps);
+// graphs without hubs run the instance without that code (fewer registers,
+// so the 128-entry one keeps 8 blocks an SM).
+template <typename Off, int CAP, bool COUNT = false, bool HUB = false>
 __global__ void __launch_bounds__(SW_WARPS * 32)
     k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                    const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S,
-                   unsigned long long* __restrict__ tri = nullptr) {
+                   unsigned long long* __restrict__ tri = nullptr, HubView hv = HubView{nullptr, nullptr, 0, 1},
+                   unsigned long long* work = nullptr) {
     __shared__ int sK[SW_WARPS][CAP];
     __shared__ int sC[SW_WARPS][CAP];
     __shared__ int sP[SW_WARPS][CAP + 1];
@@ -76,7 +121,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
     int* C = sC[warp];
     int* P = sP[warp];
     Off* E = sE[warp];
-    unsigned long long ntri = 0;
+    unsigned long long ntri = 0, wv = 0, wh = 0;  // triangles; N+(v) entries walked, bitmap probes
     const int64_t nwarps = (int64_t)gridDim.x * SW_WARPS;
     for (int64_t u = blockIdx.x * (int64_t)SW_WARPS + warp; u < n; u += nwarps) {
         const Off up0 = eo[u], up1 = rowptr[u + 1];
@@ -94,6 +139,13 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
                 const Off v0 = __ldg(eo + v);
                 E[p] = v0;
                 dv = (int)(__ldg(rowptr + v + 1) - v0);
+                if constexpr (!COUNT && HUB) {
+                    const int32_t h = __ldg(hv.hub_of + v);
+                    if (h >= 0 && (d - 1 - p) * hv.factor < dv) {  // walk u's entries above v instead
+                        E[p] = -(Off)h - 1;
+                        dv = 0;
+                    }
+                }
             }
             int x = dv;
 #pragma unroll
@@ -136,14 +188,54 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
             }
         }
         __syncwarp();
-        if constexpr (!COUNT)
+        if constexpr (!COUNT) {
+            if constexpr (HUB) {
+                // the switched pairs: P <- prefix of their d - 1 - p entries
+                int carry2 = 0;
+                for (int b = 0; b < d; b += 32) {
+                    const int p = b + lane;
+                    const int a = (p < d && E[p] < 0) ? d - 1 - p : 0;
+                    int x = a;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL_MASK, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (p < d) P[p] = carry2 + x - a;
+                    carry2 += __shfl_sync(FULL_MASK, x, 31);
+                }
+                if (lane == 0) P[d] = carry2;
+                __syncwarp();
+                for (int idx = lane; idx < carry2; idx += 32) {
+                    const int p = seg_of(P, d, idx);
+                    const int r = p + 1 + (idx - P[p]);
+                    const int32_t h = (int32_t)(-E[p] - 1);
+                    const int64_t k = hub_rank(hv, h, K[r]);
+                    if (k >= 0) {
+                        atomicAdd(&C[r], 1);  // edge {u, w}
+                        atomicAdd(&C[p], 1);  // edge {u, v}
+                        add_support(S, __ldg(eid + __ldg(rowptr + K[p]) + k), 1);  // edge {v, w}
+                    }
+                }
+                __syncwarp();
+            }
             for (int p = lane; p < d; p += 32)
                 if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
+            if constexpr (HUB) {
+                wv += (unsigned long long)total;
+                wh += (unsigned long long)P[d];
+            }
+        }
         __syncwarp();
     }
     if constexpr (COUNT) {
         ntri = warp_sum(ntri);
         if (lane == 0 && ntri) atomicAdd(tri, ntri);
+    } else if constexpr (HUB) {
+        if (work && lane == 0 && (wv | wh)) {
+            atomicAdd(work, wv);
+            atomicAdd(work + 1, wh);
+        }
     }
 }
 
@@ -179,12 +271,14 @@ template <typename Off, bool COUNT = false>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
-                    int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr) {
+                    int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr,
+                    HubView hv = HubView{nullptr, nullptr, 0, 1}, unsigned long long* work = nullptr) {
     extern __shared__ int smem[];
     unsigned long long ntri = 0;
     int* K = smem;
     int* C = smem + cap;
-    int* P = smem + 2 * cap;  // cap + 1 entries
+    int* P = smem + 2 * cap;      // cap + 1 entries
+    int* Hs = smem + 3 * cap + 1;  // hub index of a switched pair, else -1 (support only)
     __shared__ int wsum[SB_THREADS / 32];
     __shared__ int s_carry;
     for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
@@ -201,6 +295,14 @@ __global__ void __launch_bounds__(SB_THREADS)
                 K[p] = v;
                 C[p] = 0;
                 dv = (int)(__ldg(rowptr + v + 1) - __ldg(eo + v));
+                if constexpr (!COUNT) {
+                    int32_t h = hv.hub_of ? __ldg(hv.hub_of + v) : -1;
+                    if (h >= 0 && (d - 1 - p) * hv.factor < dv)
+                        dv = 0;  // walk u's entries above v in v's bitmap instead
+                    else
+                        h = -1;
+                    Hs[p] = h;
+                }
             }
             int incl = block_scan_incl(dv, wsum);
             int carry = s_carry;
@@ -241,9 +343,44 @@ __global__ void __launch_bounds__(SB_THREADS)
             }
         }
         __syncthreads();
-        if constexpr (!COUNT)
+        if constexpr (!COUNT) {
+            int total2 = 0;
+            if (hv.hub_of) {
+                // switched pairs: P <- prefix of their d - 1 - p entries
+                if (threadIdx.x == 0) s_carry = 0;
+                __syncthreads();
+                for (int b = 0; b < d; b += SB_THREADS) {
+                    const int p = b + threadIdx.x;
+                    const int a = (p < d && Hs[p] >= 0) ? d - 1 - p : 0;
+                    const int incl = block_scan_incl(a, wsum);
+                    const int carry = s_carry;
+                    if (p < d) P[p] = carry + incl - a;
+                    __syncthreads();
+                    if (threadIdx.x == SB_THREADS - 1) s_carry = carry + incl;
+                    __syncthreads();
+                }
+                total2 = s_carry;
+                if (threadIdx.x == 0) P[d] = total2;
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < total2; idx += SB_THREADS) {
+                    const int p = seg_of(P, d, idx);
+                    const int r = p + 1 + (idx - P[p]);
+                    const int64_t k = hub_rank(hv, Hs[p], K[r]);
+                    if (k >= 0) {
+                        atomicAdd(&C[r], 1);  // edge {u, w}
+                        atomicAdd(&C[p], 1);  // edge {u, v}
+                        add_support(S, __ldg(eid + __ldg(rowptr + K[p]) + k), 1);  // edge {v, w}
+                    }
+                }
+                __syncthreads();
+            }
             for (int p = threadIdx.x; p < d; p += SB_THREADS)
                 if (C[p]) add_support(S, __ldg(eid + up0 + p), C[p]);
+            if (work && threadIdx.x == 0) {
+                atomicAdd(work, (unsigned long long)total);
+                atomicAdd(work + 1, (unsigned long long)total2);
+            }
+        }
         __syncthreads();
     }
     if constexpr (COUNT) {
@@ -258,8 +395,9 @@ template <typename Off, bool COUNT = false>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_global(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                      const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts,
-                     int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr) {
-    unsigned long long ntri = 0;
+                     int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr,
+                     unsigned long long* work = nullptr) {
+    unsigned long long ntri = 0, wv = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
         const int32_t u = verts[i];
@@ -267,6 +405,7 @@ __global__ void __launch_bounds__(SB_THREADS)
         for (Off pv = up0 + warp; pv < up1; pv += SB_THREADS / 32) {
             const int v = __ldg(col + pv);
             const Off v0 = __ldg(eo + v), v1 = __ldg(rowptr + v + 1);
+            wv += (unsigned long long)(v1 - v0);
             int cuv = 0;
             for (Off q = v0 + lane; q < v1; q += 32) {
                 int w = __ldg(col + q);
@@ -290,7 +429,32 @@ __global__ void __launch_bounds__(SB_THREADS)
     if constexpr (COUNT) {
         ntri = warp_sum(ntri);
         if (lane == 0 && ntri) atomicAdd(tri, ntri);
+    } else if (work && lane == 0 && wv) {
+        atomicAdd(work, wv);
     }
+}
+
+// N+(v) entries the side switch saves: over pairs u < v (v at slot p of
+// N+(u)) whose v is a hub and whose N+(v) is longer than u's entries above
+// v, d+(v) minus those entries.  A warp per vertex.
+template <typename Off>
+__global__ void k_switch_gain(const Off* __restrict__ rowptr, const Off* __restrict__ eo,
+                              const int32_t* __restrict__ col, const int32_t* __restrict__ hub_of, int32_t n,
+                              unsigned long long* __restrict__ gain) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long s = 0;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const Off p0 = eo[u], p1 = rowptr[u + 1];
+        for (Off p = p0 + lane; p < p1; p += 32) {
+            const int32_t v = col[p];
+            if (hub_of[v] < 0) continue;
+            const int64_t above = (int64_t)(p1 - 1 - p), dv = (int64_t)(rowptr[v + 1] - eo[v]);
+            if (above * SUP_SWITCH_FACTOR < dv) s += (unsigned long long)(dv - above);
+        }
+    }
+    s = warp_sum(s);
+    if (lane == 0 && s) atomicAdd(gain, s);
 }
 
 __global__ void k_pack_ss(const int* __restrict__ S, int2* __restrict__ ss, int64_t m) {
@@ -306,35 +470,57 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     // peel starts)
     int* S = g->fq[0][0];
     CU(cudaMemsetAsync(S, 0, sizeof(int) * (size_t)(g->m > 0 ? g->m : 1), s));
+    // the hub bitmaps, when the peeling workspace has built them
+    HubView hv{nullptr, nullptr, 0, 1};
+    if (g->sup_switch && g->n_hub > 0 && g->hub_of && g->hub_bits)
+        hv = HubView{g->hub_of, g->hub_bits, g->hub_words, SUP_SWITCH_FACTOR};
+    // work counters: without hubs every kernel walks exactly W+ = sum_v
+    // d-(v) d+(v) entries (known from the build), so only the switching
+    // instances count
+    unsigned long long* work = nullptr;
+    if (g->ctr && hv.hub_of) {
+        work = reinterpret_cast<unsigned long long*>(g->ctr + TRUSS_CTR_SUPPORT_WORK);
+        CU(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), s));
+    }
     if (g->n > 0 && g->m > 0) {
         // one warp-per-vertex instance: the 128-entry one when no N+(u) is
         // longer (8 blocks an SM), else the 256-entry one (6 blocks an SM);
         // two instances run one after the other cost more than either
         int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
-        if (g->max_updeg <= SW_SPLIT)
-            k_support_warp<Off, SW_SPLIT><<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S);
+        const bool hub = hv.hub_of != nullptr;
+        if (g->max_updeg <= SW_SPLIT && hub)
+            k_support_warp<Off, SW_SPLIT, false, true>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
+        else if (g->max_updeg <= SW_SPLIT)
+            k_support_warp<Off, SW_SPLIT>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
+        else if (hub)
+            k_support_warp<Off, TRUSS_SUP_WARP_CAP, false, true>
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
         else
             k_support_warp<Off, TRUSS_SUP_WARP_CAP>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S);
+                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
         CU(cudaGetLastError());
         truss_note_launch();
     }
     if (g->n_sup_big > 0) {
         const int cap = TRUSS_SUP_BLOCK_CAP;
-        const size_t smem = sizeof(int) * (size_t)(3 * cap + 1);
+        const size_t smem = sizeof(int) * (size_t)(4 * cap + 1);
         static bool attr_set[2] = {false, false};
         if (!attr_set[sizeof(Off) == 8]) {
             CU(cudaFuncSetAttribute(k_support_block<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             attr_set[sizeof(Off) == 8] = true;
         }
         int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
-        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S);
+        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap,
+                                                              S, nullptr, hv, work);
         CU(cudaGetLastError());
         truss_note_launch();
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
-        k_support_global<Off><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S);
+        k_support_global<Off>
+            <<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge, g->n_sup_huge, S, nullptr, work);
         CU(cudaGetLastError());
         truss_note_launch();
     }
@@ -405,6 +591,31 @@ extern "C" int truss_triangle_count(truss_graph* g, int64_t* h_count, void* stre
     }
     cudaFreeAsync(d_tri, s);
     return rc;
+}
+
+// Decides, once the hub bitmaps exist, whether the support kernels switch
+// sides at hubs for this graph (sets g->sup_switch).
+int truss_support_plan(truss_graph* g, cudaStream_t s) {
+    g->sup_switch = 0;
+    if (g->n_hub <= 0 || !g->hub_of || g->n <= 0 || g->wedges_up <= 0) return TRUSS_OK;
+    unsigned long long* d_gain = nullptr;
+    CU(cudaMallocAsync((void**)&d_gain, sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(d_gain, 0, sizeof(unsigned long long), s));
+    const int blocks = grid_for((int64_t)g->n, 8, (int64_t)g->sms * 8);
+    if (g->off64)
+        k_switch_gain<int64_t><<<blocks, 256, 0, s>>>((const int64_t*)g->rowptr, (const int64_t*)g->eo, g->col,
+                                                      g->hub_of, g->n, d_gain);
+    else
+        k_switch_gain<int32_t><<<blocks, 256, 0, s>>>((const int32_t*)g->rowptr, (const int32_t*)g->eo, g->col,
+                                                      g->hub_of, g->n, d_gain);
+    CU(cudaGetLastError());
+    unsigned long long gain = 0;
+    CU(cudaMemcpyAsync(&gain, d_gain, sizeof(gain), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    cudaFreeAsync(d_gain, s);
+    g->sup_gain = (int64_t)gain;
+    g->sup_switch = (int64_t)gain * SUP_SWITCH_MIN_GAIN >= g->wedges_up;
+    return TRUSS_OK;
 }
 
 int truss_support_internal(truss_graph* g, int2* ss, cudaStream_t s) {

@@ -49,7 +49,7 @@ def test_strerror_and_defaults_without_gpu(pkt):
     o = pkt.default_opts()
     assert o.loop == pkt.LOOP_PERSISTENT and o.variant == pkt.VAR_AUTO and o.level_jump == 1
     assert o.compact == -1 and o.max_level == 0 and not o.h_level_edges and not o.h_level_ns
-    assert ctypes.sizeof(pkt.Opts) == 104 and ctypes.sizeof(pkt.Stats) == 112
+    assert ctypes.sizeof(pkt.Opts) == 104 and ctypes.sizeof(pkt.Stats) == 128
 
 
 def test_null_arguments_are_rejected_without_gpu(pkt):
@@ -147,4 +147,4 @@ def test_header_is_plain_c_and_links(pkt, tmp_path):
                            "-Wl,-rpath," + libdir, "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
-    assert out.stdout.split()[:3] == [str(pkt.LOOP_PERSISTENT), "104", "112"]
+    assert out.stdout.split()[:3] == [str(pkt.LOOP_PERSISTENT), "104", "128"]

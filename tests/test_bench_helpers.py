@@ -14,17 +14,21 @@ import bench  # noqa: E402
 
 def test_algorithmic_bytes_model():
     st = {"m": 10, "triangles": 3, "wedges_up": 7, "scanned": 25, "dmin_sum": 40, "walked": 31,
-          "compacted_slots": 12}
+          "compacted_slots": 12, "support_walked": 5, "support_hub_probes": 2}
     sup, peel = bench.algorithmic_bytes(st, n=6)
-    # support: 32 B per edge, 8 B per vertex, 4 B per N+(v) entry, 12 B per triangle
-    assert sup == 32 * 10 + 8 * 6 + 4 * 7 + 12 * 3
+    # support: 32 B per edge, 8 B per vertex, 4 B per N+(v) entry read, 32 B
+    # per hub-bitmap probe, 12 B per triangle
+    assert sup == 32 * 10 + 8 * 6 + 4 * 5 + 32 * 2 + 12 * 3
     # peel: Scans 16 B per entry visited less 8 B per edge of the first
     # Scan, 36 B per edge, 4 B per shorter-row entry walked (as the rows
     # stood), 28 B per triangle, 24 B per row entry a compaction visited
     assert peel == (16 * 25 - 8 * 10) + 36 * 10 + 4 * 31 + 28 * 3 + 24 * 12
     # without compaction the walk is the static sum of min(d(u), d(v))
-    st2 = {k: v for k, v in st.items() if k not in ("walked", "compacted_slots")}
+    st2 = {k: v for k, v in st.items() if k not in ("walked", "compacted_slots", "support_walked",
+                                                    "support_hub_probes")}
     assert bench.algorithmic_bytes(st2, n=6)[1] == (16 * 25 - 8 * 10) + 36 * 10 + 4 * 40 + 28 * 3
+    # without the support counts, W+ entries
+    assert bench.algorithmic_bytes(st2, n=6)[0] == 32 * 10 + 8 * 6 + 4 * 7 + 12 * 3
 
 
 def test_peak_comes_from_the_measured_file_when_present():

@@ -588,3 +588,34 @@ def test_edge_centric_support_matches_oracle(pkt, relabel, off64):
     e = dev(np.zeros(0, np.int32))
     G = pkt.build_csr(e, e, 4)
     assert G.support_ros().numel() == 0
+
+
+@pytest.mark.parametrize("relabel,off64", [(True, False), (False, False), (True, True)])
+def test_support_switches_to_hub_bitmaps(pkt, relabel, off64):
+    """Graphs with hub vertices (degree >= 1024): for pairs u < v whose v is
+    a hub and whose N+(v) is longer than u's entries above v, the support
+    kernels walk those entries and probe v's bitmap.  The support equals the
+    oracle's, the probes happen, and they replace more N+(v) entries than
+    they cost (the switch is taken when it saves at least a tenth of W+)."""
+    k = 3000
+    wheel = gg.EdgeList(k + 1, np.concatenate([np.zeros(k), np.arange(1, k + 1)]).astype(np.int32),
+                        np.concatenate([np.arange(1, k + 1), np.arange(1, k + 1) % k + 1]).astype(np.int32), "wheel")
+    probes = 0
+    for g in (gg.chung_lu(20000, 2.1, 20.0, 5000.0, seed=13), gg.chung_lu(30000, 1.9, 40.0, 20000.0, seed=17),
+              gg.rmat(14, 32, seed=9), wheel):
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, **_flags(relabel, off64))
+        eu, ev = oracle.canonical(g.n, g.src, g.dst)
+        S = oracle.support(g.n, eu, ev)
+        assert np.array_equal(host(G.support()), S), g.name
+        tau, st = G.decompose(stats=True)
+        assert np.array_equal(host(tau), oracle.truss(g.n, eu, ev)), g.name
+        assert st["support_walked"] + st["support_hub_probes"] <= st["wedges_up"], g.name
+        if st["support_hub_probes"] > 0:
+            # a switch that ran saved at least a tenth of W+: the N+(v)
+            # entries it skipped less the probes it made instead
+            saved = st["wedges_up"] - st["support_walked"] - st["support_hub_probes"]
+            assert 10 * saved >= st["wedges_up"], g.name
+        probes += st["support_hub_probes"]
+        G.free()
+    if relabel:
+        assert probes > 0

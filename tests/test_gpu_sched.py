@@ -106,8 +106,8 @@ def test_learned_choice_regret_on_held_out_sublevels(pkt):
     every sub-level's time under each variant is measured, and the model's
     choices are scored by regret (time above the per-sub-level best).  The
     trained model must do better than its untrained start, no worse than the
-    worst fixed variant, and (within timing noise) no worse than the default
-    mapping; the regrets are printed."""
+    worst fixed variant, and strictly better than the default mapping; the
+    regrets are printed."""
     import torch
 
     train = [gg.rgg2d(1 << 18, 32.0, seed=51), gg.chung_lu(1 << 18, 2.1, 20.0, 4096.0, seed=52)]
@@ -145,6 +145,7 @@ def test_learned_choice_regret_on_held_out_sublevels(pkt):
     assert r_learned <= max(r_fixed)
     assert r_learned <= r_untrained + 1e-9 or r_untrained == 0
     # against the method without it (the default mapping, half a warp per
-    # light edge), allowing 2 % of the best total for timing noise
-    assert r_learned <= r_fixed[1] + 0.02 * best, (r_learned, r_fixed)
+    # light edge): the trained model must choose strictly better on these
+    # held-out sub-levels (every choice is scored on the same measured times)
+    assert r_learned < r_fixed[1], (r_learned, r_fixed)
     torch.cuda.synchronize()
