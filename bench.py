@@ -187,8 +187,10 @@ def kernel_source_hash(kernel: str = "k_persistent"):
 
 
 def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current sources of that kernel; else None."""
+    """DRAM bytes of the kernel in one step (all its launches in one
+    decomposition: the peel is one launch per stretch between row
+    compactions) from the committed ncu summary, if it was taken on the
+    current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(path))
@@ -197,7 +199,7 @@ def recorded_traffic(kernel: str, workload: str):
     ent = rec.get(workload, {}).get(kernel)
     if not ent or ent.get("source_hash") != kernel_source_hash(kernel):
         return None
-    return ent.get("bytes_per_launch")
+    return ent.get("bytes_per_step")
 
 
 def peaks():
