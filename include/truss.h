@@ -351,9 +351,12 @@ TRUSS_API void truss_default_opts(truss_opts* opts);
  * >= k-2 triangles of edges of trussness >= k" this proves the result exact.
  *   stats   : may be NULL; filled only when opts->sync is set.
  * Workspace: the first call on a graph allocates its peeling workspace and
- * keeps it until truss_free (roughly 100 to 150 bytes per edge with int32 offsets,
- * plus neighbour bitmaps of its highest-degree vertices within 128 bytes per
- * edge and 32 GiB); TRUSS_ENOMEM when the device cannot hold it.
+ * keeps it until truss_free (roughly 100 to 150 bytes per edge with int32
+ * offsets, plus neighbour bitmaps of its vertices of degree >= 1024 -- the
+ * threshold doubles until the bitmaps fit 1024 bytes per edge and 3/4 of the
+ * device memory free at that moment -- plus, for graphs that compact their
+ * rows, about 60 bytes per edge more); TRUSS_ENOMEM when the device cannot
+ * hold the rest.
  */
 TRUSS_API int truss_decompose(truss_graph* g, int32_t* d_truss, const truss_opts* opts, truss_stats* stats, void* stream);
 

@@ -2292,19 +2292,30 @@ int peel_sublevel_impl(truss_graph* g, int32_t* d_S, uint8_t* d_flags, const int
 
 }  // namespace
 
-// Hub bitmaps for the vertices of degree >= thr, thr = 1024 doubled until
-// they fit a budget of 128 bytes per edge (at most 32 GiB): 32 bytes per 192
-// vertex ids for each hub.  On R-MAT scale 24 the
-// peel takes 3.65 s with the 32 GiB budget, 4.02 s with 8 GiB.
+// Hub bitmaps for the vertices of degree >= thr, thr = HUB_MIN_DEG doubled
+// until they fit the budget: 32 bytes per 192 vertex ids for each hub, at
+// most HUB_BYTES_PER_EDGE per edge and HUB_FREE_SHARE of the device memory
+// free when the workspace is built; when their allocation fails all the
+// same, thr doubles again.  The bitmaps serve the peel's probes of long rows
+// and the support's side switch.  R-MAT scale 24 (hubs of degree >= 8192 /
+// 4096 / 2048: 6 / 34 / 144 GiB of bitmaps): support 1.07 / 0.70 / 0.49 s,
+// peel 1.21 / 0.98 / 0.84 s; Chung-Lu 2^20 (1602 hubs of degree >= 1024,
+// 0.3 GiB) and the batch are fastest with HUB_MIN_DEG = 1024.
+constexpr int64_t HUB_MIN_DEG = 1024;
+constexpr int64_t HUB_BYTES_PER_EDGE = 1024;
+constexpr double HUB_FREE_SHARE = 0.75;
+
 template <typename Off>
 int build_hubs(truss_graph* g, cudaStream_t s) {
     const Off* rowptr = (const Off*)g->rowptr;
     const int64_t hw = (((int64_t)g->n + 191) / 192) * 4;
     const int64_t per_hub = hw * 8;
-    const int64_t budget = std::min<int64_t>((int64_t)32 << 30, 128 * g->m);
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t budget = std::min<int64_t>(HUB_BYTES_PER_EDGE * g->m, (int64_t)((double)free_b * HUB_FREE_SHARE));
     int* d_cnt = nullptr;
     CU(cudaMallocAsync((void**)&d_cnt, sizeof(int), s));
-    int64_t thr = 1024;
+    int64_t thr = HUB_MIN_DEG;
     int cnt = 0;
     for (;;) {
         CU(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
@@ -2312,7 +2323,15 @@ int build_hubs(truss_graph* g, cudaStream_t s) {
         CU(cudaGetLastError());
         CU(cudaMemcpyAsync(&cnt, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        if ((int64_t)cnt * per_hub <= budget) break;
+        if ((int64_t)cnt * per_hub <= budget) {
+            if (cnt == 0) break;
+            // reserve the bitmaps now; when the device cannot hold them, fewer hubs
+            if (cudaMallocAsync((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw), s) ==
+                cudaSuccess)
+                break;
+            cudaGetLastError();  // clear the failed allocation
+            g->hub_bits = nullptr;
+        }
         thr *= 2;
     }
     g->n_hub = cnt;
@@ -2321,7 +2340,6 @@ int build_hubs(truss_graph* g, cudaStream_t s) {
         int32_t* hub_vert = nullptr;
         CU(cudaMallocAsync((void**)&g->hub_of, sizeof(int32_t) * (size_t)g->n, s));
         CU(cudaMallocAsync((void**)&hub_vert, sizeof(int32_t) * (size_t)cnt, s));
-        CU(cudaMallocAsync((void**)&g->hub_bits, sizeof(unsigned long long) * (size_t)(cnt * hw), s));
         CU(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
         CU(cudaMemsetAsync(g->hub_bits, 0, sizeof(unsigned long long) * (size_t)(cnt * hw), s));
         k_hub_list<Off><<<grid_for(g->n, 256), 256, 0, s>>>(rowptr, g->n, thr, g->hub_of, hub_vert, d_cnt);

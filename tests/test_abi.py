@@ -62,6 +62,9 @@ def test_null_arguments_are_rejected_without_gpu(pkt):
     assert lib.truss_num_edges(None, ctypes.byref(m)) == pkt.EINVAL
     assert lib.truss_decompose(None, None, None, None, None) == pkt.EINVAL
     assert lib.truss_support(None, None, None) == pkt.EINVAL
+    assert lib.truss_support_ros(None, None, None) == pkt.EINVAL
+    sw, up = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.truss_decompose_local(None, None, 0, ctypes.byref(sw), ctypes.byref(up), None) == pkt.EINVAL
 
 
 def test_no_oracle_in_product_path():
