@@ -154,6 +154,9 @@ WORKLOADS = {
     "chunglu_n2^20_d20": (lambda s: chung_lu(1 << 20, 2.1, 20.0, float(1 << 14), s), 2),
     "rgg2d_n2^21_d32": (lambda s: rgg2d(1 << 21, 32.0, s), 3),
     "rmat24_ef16": (lambda s: rmat(24, 16, seed=s), 4),
+    # the R-MAT scale-24 generator at 1/8 of its size: a case small enough
+    # for a full profiler capture of the same kernels
+    "rmat21_ef16": (lambda s: rmat(21, 16, seed=s), 4),
 }
 BATCH_WORKLOAD = "chunglu_batch4096"
 

@@ -475,6 +475,18 @@ TRUSS_API int truss_autotune(truss_graph* g, int8_t* h_table, int32_t repeats, v
  * latched device-side error (and clear it). */
 TRUSS_API int truss_sync(truss_graph* g, void* stream);
 
+/* truss_pool_keep -- how many bytes of freed device memory the stream-ordered
+ * pool the library allocates from (this process's default pool on the
+ * current device) keeps for reuse instead of returning it to the driver
+ * (the library's default: 16 GiB, set by its first graph build).  Keeping
+ * more saves mapping the memory again when graph after graph is built and
+ * freed (R-MAT scale 24 through truss_decompose_host: 2.19 s a call with
+ * 16 GiB kept, 1.99 s with 200 GB); the memory kept is not available to
+ * other allocators in the process (cudaMalloc, frameworks' caching
+ * allocators).  0 also returns what the pool holds now.  The paper has no
+ * counterpart.  TRUSS_EINVAL for a negative size. */
+TRUSS_API int truss_pool_keep(int64_t bytes);
+
 /* ---------------------------------------------- allocation-free support */
 
 /* Largest vertex count truss_support_noalloc accepts. */

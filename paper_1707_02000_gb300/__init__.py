@@ -40,7 +40,7 @@ EXPORTS = (
     "truss_peel_sublevel", "truss_decompose_host", "truss_sync", "truss_support_noalloc",
     "truss_decompose_batch", "truss_sched_features", "truss_sched_init", "truss_sched_grad",
     "truss_sched_train", "truss_sched_predict", "truss_autotune", "truss_ktruss_components",
-    "truss_triangle_count", "truss_support_ros", "truss_decompose_local",
+    "truss_triangle_count", "truss_support_ros", "truss_decompose_local", "truss_pool_keep",
 )
 
 
@@ -94,6 +94,7 @@ def _declare(lib):
     lib.truss_csr_copy.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.truss_support.argtypes = [vp, vp, vp]
     lib.truss_support_ros.argtypes = [vp, vp, vp]
+    lib.truss_pool_keep.argtypes = [i64]
     lib.truss_decompose_local.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     lib.truss_ktruss_components.argtypes = [vp, vp, i32, vp, vp, vp]
     lib.truss_triangle_count.argtypes = [vp, vp, vp]
@@ -353,6 +354,12 @@ def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = Fal
     _check(_lib.truss_build_csr(_dptr(src) if k else None, _dptr(dst) if k else None, k, n, flags,
                                 _stream(stream), ctypes.byref(h)), "truss_build_csr")
     return Graph(h)
+
+
+def pool_keep(nbytes: int):
+    """Bytes of freed device memory the library's stream-ordered pool keeps
+    for reuse on the current device (truss_pool_keep)."""
+    _check(_lib.truss_pool_keep(int(nbytes)), "truss_pool_keep")
 
 
 def decompose_host(src: np.ndarray, dst: np.ndarray, n: int, degree_order: bool = True, offsets64: bool = False,

@@ -587,17 +587,32 @@ void truss_free_device(truss_graph* g) {
 // The library allocates from this process's default stream-ordered pool.
 // Its release threshold (default 0) returns freed memory to the driver at
 // every synchronisation, so each new graph would map its buffers again; keep
-// up to 16 GiB of freed pool memory for reuse instead.  The attribute belongs
-// to this process's pool and ends with it.
+// up to 16 GiB of freed pool memory for reuse instead (truss_pool_keep sets
+// another amount).  The attribute belongs to this process's pool and ends
+// with it.
+static bool g_pool_set[64] = {};
+
 static void keep_pool_memory(int device) {
-    static bool done[64] = {};
-    if (device < 0 || device >= 64 || done[device]) return;
+    if (device < 0 || device >= 64 || g_pool_set[device]) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t keep = (uint64_t)16 << 30;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    done[device] = true;
+    g_pool_set[device] = true;
+}
+
+extern "C" int truss_pool_keep(int64_t bytes) {
+    if (bytes < 0) return TRUSS_EINVAL;
+    int device = 0;
+    CU(cudaGetDevice(&device));
+    cudaMemPool_t pool;
+    CU(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t keep = (uint64_t)bytes;
+    CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    if (bytes == 0) CU(cudaMemPoolTrimTo(pool, 0));
+    if (device >= 0 && device < 64) g_pool_set[device] = true;
+    return TRUSS_OK;
 }
 
 extern "C" int truss_build_csr(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t n, uint32_t flags,

@@ -1392,22 +1392,30 @@ __global__ void k_hub_fill(const Off* __restrict__ rowptr, const int32_t* __rest
     }
 }
 
-// per hub: word 0 of each block <- neighbours in the blocks before it
+// per hub: word 0 of each block <- neighbours in the blocks before it.  A
+// block takes a hub; each thread owns HPRE consecutive 32-byte blocks a
+// round (their counts kept in registers), one block-wide scan a round.
+constexpr int HPRE = 8;
+
 __global__ void k_hub_pre(unsigned long long* __restrict__ bits, int32_t nhub, int64_t hw) {
     __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
     const int64_t nb = hw >> 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int32_t h = blockIdx.x; h < nhub; h += gridDim.x) {
         unsigned long long* B = bits + (int64_t)h * hw;
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (int64_t base = 0; base < nb; base += blockDim.x) {
-            const int64_t b = base + threadIdx.x;
-            uint32_t c = 0;
-            if (b < nb)
-                for (int k = 1; k < 4; k++) c += (uint32_t)__popcll(B[b * 4 + k]);
-            uint32_t x = c;
+        uint32_t carry = 0;
+        for (int64_t base = 0; base < nb; base += (int64_t)blockDim.x * HPRE) {
+            const int64_t b0 = base + (int64_t)threadIdx.x * HPRE;
+            uint32_t c[HPRE];
+            uint32_t tot = 0;
+#pragma unroll
+            for (int k = 0; k < HPRE; k++) {
+                const int64_t b = b0 + k;
+                c[k] = b < nb ? (uint32_t)(__popcll(B[4 * b + 1]) + __popcll(B[4 * b + 2]) + __popcll(B[4 * b + 3]))
+                              : 0u;
+                tot += c[k];
+            }
+            uint32_t x = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(FULL_MASK, x, o);
@@ -1415,16 +1423,25 @@ __global__ void k_hub_pre(unsigned long long* __restrict__ bits, int32_t nhub, i
             }
             if (lane == 31) wsum[warp] = x;
             __syncthreads();
-            uint32_t before = carry;
-            for (int w2 = 0; w2 < warp; w2++) before += wsum[w2];
-            if (b < nb) B[b * 4] = before + x - c;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t t = 0;
-                for (int w2 = 0; w2 < nwarp; w2++) t += wsum[w2];
-                carry += t;
+            if (warp == 0) {
+                uint32_t w = lane < nwarp ? wsum[lane] : 0u;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL_MASK, w, o);
+                    if (lane >= o) w += y;
+                }
+                if (lane < nwarp) wsum[lane] = w;
             }
             __syncthreads();
+            uint32_t before = carry + (warp ? wsum[warp - 1] : 0u) + x - tot;
+#pragma unroll
+            for (int k = 0; k < HPRE; k++) {
+                const int64_t b = b0 + k;
+                if (b < nb) B[4 * b] = before;
+                before += c[k];
+            }
+            carry += wsum[nwarp - 1];
+            __syncthreads();  // wsum is rewritten next round
         }
     }
 }

@@ -65,6 +65,7 @@ def test_null_arguments_are_rejected_without_gpu(pkt):
     assert lib.truss_support_ros(None, None, None) == pkt.EINVAL
     sw, up = ctypes.c_int64(), ctypes.c_int64()
     assert lib.truss_decompose_local(None, None, 0, ctypes.byref(sw), ctypes.byref(up), None) == pkt.EINVAL
+    assert lib.truss_pool_keep(-1) == pkt.EINVAL
 
 
 def test_no_oracle_in_product_path():

@@ -619,3 +619,17 @@ def test_support_switches_to_hub_bitmaps(pkt, relabel, off64):
         G.free()
     if relabel:
         assert probes > 0
+
+
+def test_pool_keep_setting(pkt):
+    """The pool retention setting changes nothing but memory reuse: builds
+    and decompositions around each setting stay exact."""
+    g = gg.chung_lu(20000, 2.1, 20.0, 5000.0, seed=13)
+    want = oracle.truss_of_edges(g.n, g.src, g.dst)[2]
+    for keep in (0, 1 << 34, 16 << 30):
+        pkt.pool_keep(keep)
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n)
+        assert np.array_equal(host(G.decompose()), want), keep
+        G.free()
+        tau, _ = pkt.decompose_host(g.src, g.dst, g.n)
+        assert np.array_equal(tau, want), keep
