@@ -42,12 +42,12 @@ def test_peak_comes_from_the_measured_file_when_present():
 
 def test_recorded_traffic_is_keyed_to_the_kernel_sources(monkeypatch):
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-    ent = rec["chunglu_n2^20_d20"]["k_persistent"]
+    ent = rec[bench.WORKLOAD]["k_persistent"]
     if ent["source_hash"] == bench.kernel_source_hash("k_persistent"):
-        assert bench.recorded_traffic("k_persistent", "chunglu_n2^20_d20") == ent["bytes_per_step"]
+        assert bench.recorded_traffic("k_persistent", bench.WORKLOAD) == ent["bytes_per_step"]
     # any change to the sources makes the record stale
     monkeypatch.setattr(bench, "kernel_source_hash", lambda kernel="k_persistent": "0" * 16)
-    assert bench.recorded_traffic("k_persistent", "chunglu_n2^20_d20") is None
+    assert bench.recorded_traffic("k_persistent", bench.WORKLOAD) is None
     assert bench.recorded_traffic("k_persistent", "no_such_workload") is None
 
 
