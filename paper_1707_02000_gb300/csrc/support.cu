@@ -58,6 +58,30 @@ __device__ __forceinline__ int seg_of(const int* P, int d, int idx) {
     return lo;
 }
 
+// Segment of idx given the segment p of an earlier index of the same flat
+// range (P[p] <= idx, segments only move forward): the largest q >= p with
+// P[q] <= idx, found by steps of 1, 2, 4, ... from p and a binary search in
+// the last step, so a lane that moves a few segments pays a few reads
+// instead of a full search.  P[d] is the range's length, above idx.
+__device__ __forceinline__ int seg_advance(const int* P, int d, int p, int idx) {
+    if (P[p + 1] > idx) return p;
+    int lo = p + 1, hi = d - 1;  // P[lo] <= idx
+    for (int step = 1;; step <<= 1) {
+        const int probe = lo + step;
+        if (probe >= d) break;
+        if (P[probe] > idx) {
+            hi = probe - 1;
+            break;
+        }
+        lo = probe;
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P[mid] <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // First position in [lo, hi) with K[pos] >= w (K ascending); hi if none.
 __device__ __forceinline__ int lower_bound_smem(const int* K, int lo, int hi, int w) {
     while (lo < hi) {
@@ -159,12 +183,14 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
         if (lane == 0) P[d] = carry;
         __syncwarp();
         const int total = carry;
-        // two entries per lane (idx and idx + 32) with independent chains
+        // two entries per lane (idx and idx + 32) with independent chains;
+        // a lane's segment only moves forward
+        int ps = 0;
         for (int idx = lane; idx < total; idx += 64) {
             const int i2 = idx + 32;
             const bool two = i2 < total;
-            const int p1 = seg_of(P, d, idx);
-            const int p2 = two ? seg_of(P, d, i2) : p1;
+            const int p1 = ps = seg_advance(P, d, ps, idx);
+            const int p2 = two ? (ps = seg_advance(P, d, ps, i2)) : p1;
             const Off q1 = E[p1] + (idx - P[p1]);  // N+(v) starts at E[p] (staged)
             const Off q2 = two ? E[p2] + (i2 - P[p2]) : q1;
             const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
@@ -206,8 +232,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
                 }
                 if (lane == 0) P[d] = carry2;
                 __syncwarp();
+                int ps2 = 0;
                 for (int idx = lane; idx < carry2; idx += 32) {
-                    const int p = seg_of(P, d, idx);
+                    const int p = ps2 = seg_advance(P, d, ps2, idx);
                     const int r = p + 1 + (idx - P[p]);
                     const int32_t h = (int32_t)(-E[p] - 1);
                     const int64_t k = hub_rank(hv, h, K[r]);
@@ -240,6 +267,16 @@ __global__ void __launch_bounds__(SW_WARPS * 32)
 }
 
 constexpr int SB_THREADS = 1024;  // one block an SM (shared memory); 512 left it latency-bound
+constexpr int SB_WARPS = SB_THREADS / 32;
+
+// Chunk of the flat range a warp of the block kernel takes at a time: about
+// a quarter of the range per warp (so the warps finish together), between
+// 64 and 1024 indices (a lane finds its first segment by binary search once
+// per chunk and then only advances).
+__device__ __forceinline__ int sb_chunk(int total) {
+    const int c = ((total / (SB_WARPS * 4)) + 63) & ~63;
+    return c < 64 ? 64 : (c > 1024 ? 1024 : c);
+}
 
 // Block-wide inclusive scan helper for the prefix of d+(v).
 __device__ int block_scan_incl(int x, int* wsum) {
@@ -275,6 +312,7 @@ __global__ void __launch_bounds__(SB_THREADS)
                     HubView hv = HubView{nullptr, nullptr, 0, 1}, unsigned long long* work = nullptr) {
     extern __shared__ int smem[];
     unsigned long long ntri = 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* K = smem;
     int* C = smem + cap;
     int* P = smem + 2 * cap;      // cap + 1 entries
@@ -314,31 +352,53 @@ __global__ void __launch_bounds__(SB_THREADS)
         const int total = s_carry;
         if (threadIdx.x == 0) P[d] = total;
         __syncthreads();
-        // two probes per thread (idx and idx + SB_THREADS), independent chains
-        for (int idx = threadIdx.x; idx < total; idx += 2 * SB_THREADS) {
-            const int i2 = idx + SB_THREADS;
-            const bool two = i2 < total;
-            const int p1 = seg_of(P, d, idx);
-            const int p2 = two ? seg_of(P, d, i2) : p1;
-            const Off q1 = __ldg(eo + K[p1]) + (idx - P[p1]);
-            const Off q2 = two ? __ldg(eo + K[p2]) + (i2 - P[p2]) : q1;
-            const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
-            const int w2 = __ldg(col + q2), x2 = COUNT ? 0 : __ldg(eid + q2);
-            const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
-            const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
-            const bool t1 = r1 < d && K[r1] == w1, t2 = two && r2 < d && K[r2] == w2;
-            if constexpr (COUNT) {
-                ntri += (unsigned)t1 + (unsigned)t2;
-            } else {
-                if (t1) {
-                    atomicAdd(&C[r1], 1);
-                    atomicAdd(&C[p1], 1);
-                    add_support(S, x1, 1);
+        // Warps take chunks of consecutive indices (lanes 32 apart, two
+        // entries a lane in flight); a lane's segment, and the start of its
+        // N+(v) in col, change only when it crosses into the next one.
+        const int ch = sb_chunk(total);
+        for (int c0 = warp * ch; c0 < total; c0 += SB_WARPS * ch) {
+            const int cend = min(c0 + ch, total);
+            int idx = c0 + lane;
+            if (idx >= cend) continue;
+            int p = seg_of(P, d, idx);
+            Off qb = __ldg(eo + K[p]) - P[p];  // N+(v) of segment p at qb + idx
+            for (; idx < cend; idx += 64) {
+                int np = seg_advance(P, d, p, idx);
+                if (np != p) {
+                    p = np;
+                    qb = __ldg(eo + K[p]) - P[p];
                 }
-                if (t2) {
-                    atomicAdd(&C[r2], 1);
-                    atomicAdd(&C[p2], 1);
-                    add_support(S, x2, 1);
+                const int p1 = p;
+                const Off q1 = qb + idx;
+                const int i2 = idx + 32;
+                const bool two = i2 < cend;
+                if (two) {
+                    np = seg_advance(P, d, p, i2);
+                    if (np != p) {
+                        p = np;
+                        qb = __ldg(eo + K[p]) - P[p];
+                    }
+                }
+                const int p2 = p;
+                const Off q2 = two ? qb + i2 : q1;
+                const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
+                const int w2 = __ldg(col + q2), x2 = COUNT ? 0 : __ldg(eid + q2);
+                const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
+                const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
+                const bool t1 = r1 < d && K[r1] == w1, t2 = two && r2 < d && K[r2] == w2;
+                if constexpr (COUNT) {
+                    ntri += (unsigned)t1 + (unsigned)t2;
+                } else {
+                    if (t1) {
+                        atomicAdd(&C[r1], 1);
+                        atomicAdd(&C[p1], 1);
+                        add_support(S, x1, 1);
+                    }
+                    if (t2) {
+                        atomicAdd(&C[r2], 1);
+                        atomicAdd(&C[p2], 1);
+                        add_support(S, x2, 1);
+                    }
                 }
             }
         }
@@ -362,14 +422,21 @@ __global__ void __launch_bounds__(SB_THREADS)
                 total2 = s_carry;
                 if (threadIdx.x == 0) P[d] = total2;
                 __syncthreads();
-                for (int idx = threadIdx.x; idx < total2; idx += SB_THREADS) {
-                    const int p = seg_of(P, d, idx);
-                    const int r = p + 1 + (idx - P[p]);
-                    const int64_t k = hub_rank(hv, Hs[p], K[r]);
-                    if (k >= 0) {
-                        atomicAdd(&C[r], 1);  // edge {u, w}
-                        atomicAdd(&C[p], 1);  // edge {u, v}
-                        add_support(S, __ldg(eid + __ldg(rowptr + K[p]) + k), 1);  // edge {v, w}
+                const int ch2 = sb_chunk(total2);
+                for (int c0 = warp * ch2; c0 < total2; c0 += SB_WARPS * ch2) {
+                    const int cend = min(c0 + ch2, total2);
+                    int idx = c0 + lane;
+                    if (idx >= cend) continue;
+                    int p = seg_of(P, d, idx);
+                    for (; idx < cend; idx += 32) {
+                        p = seg_advance(P, d, p, idx);
+                        const int r = p + 1 + (idx - P[p]);
+                        const int64_t k = hub_rank(hv, Hs[p], K[r]);
+                        if (k >= 0) {
+                            atomicAdd(&C[r], 1);  // edge {u, w}
+                            atomicAdd(&C[p], 1);  // edge {u, v}
+                            add_support(S, __ldg(eid + __ldg(rowptr + K[p]) + k), 1);  // edge {v, w}
+                        }
                     }
                 }
                 __syncthreads();
