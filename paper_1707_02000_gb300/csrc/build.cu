@@ -244,18 +244,27 @@ __global__ void k_classify_vertices(const int64_t* __restrict__ rowptr, const in
             up = rowptr[u + 1] - eo[u];
             d = rowptr[u + 1] - rowptr[u];
         }
-        warp_append(up > TRUSS_SUP_WARP_CAP && up <= TRUSS_SUP_BLOCK_CAP, (int32_t)u, big, nbig);
+        const bool isbig = up > TRUSS_SUP_WARP_CAP && up <= TRUSS_SUP_BLOCK_CAP;
+        warp_append(isbig, (int32_t)u, big, nbig);
         warp_append(up > TRUSS_SUP_BLOCK_CAP, (int32_t)u, huge, nhuge);
+        // over the block-kernel vertices: the longest N+(u) and the widest
+        // label window above u (n - 1 - u), which size that kernel's
+        // shared-memory bitmap
+        int64_t bup = isbig ? up : 0, bwin = isbig ? (int64_t)n - 1 - u : 0;
         // one atomic per warp for each maximum (same-address atomics from
         // every vertex cost more than the rest of the kernel)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             d = max(d, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)d, o));
             up = max(up, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)up, o));
+            bup = max(bup, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)bup, o));
+            bwin = max(bwin, (int64_t)__shfl_xor_sync(FULL_MASK, (long long)bwin, o));
         }
         if ((threadIdx.x & 31) == 0) {
             if (d) atomicMax(&maxes[0], (unsigned long long)d);
             if (up) atomicMax(&maxes[1], (unsigned long long)up);
+            if (bup) atomicMax(&maxes[2], (unsigned long long)bup);
+            if (bwin) atomicMax(&maxes[3], (unsigned long long)bwin);
         }
     }
 }
@@ -505,21 +514,23 @@ int build_impl(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t
         unsigned long long* maxes = nullptr;
         CU(talloc(&big, n, s));
         CU(talloc(&huge, n, s));
-        CU(talloc(&maxes, 2, s));
-        CU(cudaMemsetAsync(maxes, 0, 2 * sizeof(unsigned long long), s));
+        CU(talloc(&maxes, 4, s));
+        CU(cudaMemsetAsync(maxes, 0, 4 * sizeof(unsigned long long), s));
         CU(cudaMemsetAsync(d_flag, 0, 4 * sizeof(int), s));
         if (n > 0)
             k_classify_vertices<<<grid_for(n, B), B, 0, s>>>(c1.rowptr, c1.eo, n, big, d_flag, huge, d_flag + 1, maxes);
         CU(cudaGetLastError());
         int h_cnt[2];
-        unsigned long long h_max[2];
+        unsigned long long h_max[4];
         CU(cudaMemcpyAsync(h_cnt, d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        CU(cudaMemcpyAsync(h_max, maxes, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(h_max, maxes, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         g->n_sup_big = h_cnt[0];
         g->n_sup_huge = h_cnt[1];
         g->max_deg = (int64_t)h_max[0];
         g->max_updeg = (int64_t)h_max[1];
+        g->sup_big_maxup = (int64_t)h_max[2];
+        g->sup_big_maxwin = (int64_t)h_max[3];
         CU(cudaMallocAsync((void**)&g->sup_big, sizeof(int32_t) * (size_t)(h_cnt[0] + 1), s));
         CU(cudaMallocAsync((void**)&g->sup_huge, sizeof(int32_t) * (size_t)(h_cnt[1] + 1), s));
         CU(cudaMemcpyAsync(g->sup_big, big, sizeof(int32_t) * (size_t)h_cnt[0], cudaMemcpyDeviceToDevice, s));

@@ -81,6 +81,8 @@ struct truss_graph {
     int32_t n_sup_big = 0;
     int32_t* sup_huge = nullptr;  // d+ > BLOCK_CAP
     int32_t n_sup_huge = 0;
+    int64_t sup_big_maxup = 0;   // over sup_big: the largest d+(u)
+    int64_t sup_big_maxwin = 0;  // over sup_big: the largest n - 1 - u
     int64_t max_deg = 0;
     int last_grid = 0, last_per_sm = 0;  // blocks of the last persistent launch
     void* gctl = nullptr;   // state of the graph-driven level loop

@@ -303,13 +303,23 @@ __device__ int block_scan_incl(int x, int* wsum) {
     return r;
 }
 
-// One block per listed vertex; cap entries of K, C, P in dynamic shared memory.
-template <typename Off, bool COUNT = false>
-__global__ void __launch_bounds__(SB_THREADS)
+// One block per listed vertex; cap entries of K, C, P, Hs in dynamic shared
+// memory.
+//
+// WIN: N+(u) is also held as a bitmap over the labels above u (bit w - u - 1;
+// nwcap 32-bit words, enough for the widest window of the listed vertices),
+// with the count of entries before each word, so a probe of w is one word
+// read (the rank only on a hit) instead of a binary search in K.  The
+// launch uses this instance when the bitmap fits shared memory, which it
+// does for degree-ordered graphs: the vertices with long N+(u) have the
+// highest labels (R-MAT scale 24: windows of at most 190,050 labels).
+template <typename Off, bool COUNT = false, bool WIN = false>
+__global__ void __launch_bounds__(SB_THREADS, WIN ? 2 : 1)
     k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
                     int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr,
-                    HubView hv = HubView{nullptr, nullptr, 0, 1}, unsigned long long* work = nullptr) {
+                    HubView hv = HubView{nullptr, nullptr, 0, 1}, unsigned long long* work = nullptr,
+                    int32_t n = 0, int nwcap = 0) {
     extern __shared__ int smem[];
     unsigned long long ntri = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -317,12 +327,17 @@ __global__ void __launch_bounds__(SB_THREADS)
     int* C = smem + cap;
     int* P = smem + 2 * cap;      // cap + 1 entries
     int* Hs = smem + 3 * cap + 1;  // hub index of a switched pair, else -1 (support only)
+    uint32_t* F = reinterpret_cast<uint32_t*>(smem + 4 * cap + 1);  // WIN: window bitmap, nwcap words
+    unsigned short* R = reinterpret_cast<unsigned short*>(F + nwcap);  // WIN: entries before each word
     __shared__ int wsum[SB_THREADS / 32];
     __shared__ int s_carry;
     for (int32_t i = blockIdx.x; i < nverts; i += gridDim.x) {
         const int32_t u = verts[i];
         const Off up0 = eo[u], up1 = rowptr[u + 1];
         const int d = (int)(up1 - up0);
+        const int nw = WIN ? (int)(((int64_t)n - 1 - u + 31) >> 5) : 0;  // <= nwcap
+        if constexpr (WIN)
+            for (int j = threadIdx.x; j < nw; j += SB_THREADS) F[j] = 0u;
         if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
         for (int b = 0; b < d; b += SB_THREADS) {
@@ -332,6 +347,10 @@ __global__ void __launch_bounds__(SB_THREADS)
                 int v = __ldg(col + up0 + p);
                 K[p] = v;
                 C[p] = 0;
+                if constexpr (WIN) {
+                    const uint32_t b = (uint32_t)(v - u - 1);
+                    atomicOr(F + (b >> 5), 1u << (b & 31));
+                }
                 dv = (int)(__ldg(rowptr + v + 1) - __ldg(eo + v));
                 if constexpr (!COUNT) {
                     int32_t h = hv.hub_of ? __ldg(hv.hub_of + v) : -1;
@@ -351,6 +370,19 @@ __global__ void __launch_bounds__(SB_THREADS)
         }
         const int total = s_carry;
         if (threadIdx.x == 0) P[d] = total;
+        if constexpr (WIN) {
+            // R[j] = entries in the words before j: a block scan over
+            // consecutive runs of words per thread
+            const int per = (nw + SB_THREADS - 1) / SB_THREADS;
+            const int j0 = min(nw, (int)threadIdx.x * per), j1 = min(nw, j0 + per);
+            int cnt = 0;
+            for (int j = j0; j < j1; ++j) cnt += __popc(F[j]);
+            int run = block_scan_incl(cnt, wsum) - cnt;
+            for (int j = j0; j < j1; ++j) {
+                R[j] = (unsigned short)run;
+                run += __popc(F[j]);
+            }
+        }
         __syncthreads();
         // Warps take chunks of consecutive indices (lanes 32 apart, two
         // entries a lane in flight); a lane's segment, and the start of its
@@ -383,9 +415,22 @@ __global__ void __launch_bounds__(SB_THREADS)
                 const Off q2 = two ? qb + i2 : q1;
                 const int w1 = __ldg(col + q1), x1 = COUNT ? 0 : __ldg(eid + q1);
                 const int w2 = __ldg(col + q2), x2 = COUNT ? 0 : __ldg(eid + q2);
-                const int r1 = lower_bound_smem(K, p1 + 1, d, w1);
-                const int r2 = lower_bound_smem(K, p2 + 1, d, w2);
-                const bool t1 = r1 < d && K[r1] == w1, t2 = two && r2 < d && K[r2] == w2;
+                int r1, r2;
+                bool t1, t2;
+                if constexpr (WIN) {
+                    // w > v > u, so w - u - 1 lies in the window
+                    const uint32_t b1 = (uint32_t)(w1 - u - 1), b2 = (uint32_t)(w2 - u - 1);
+                    const uint32_t f1 = F[b1 >> 5], f2 = F[b2 >> 5];
+                    t1 = (f1 >> (b1 & 31)) & 1u;
+                    t2 = two && ((f2 >> (b2 & 31)) & 1u);
+                    r1 = t1 ? (int)R[b1 >> 5] + __popc(f1 & ((1u << (b1 & 31)) - 1u)) : 0;
+                    r2 = t2 ? (int)R[b2 >> 5] + __popc(f2 & ((1u << (b2 & 31)) - 1u)) : 0;
+                } else {
+                    r1 = lower_bound_smem(K, p1 + 1, d, w1);
+                    r2 = lower_bound_smem(K, p2 + 1, d, w2);
+                    t1 = r1 < d && K[r1] == w1;
+                    t2 = two && r2 < d && K[r2] == w2;
+                }
                 if constexpr (COUNT) {
                     ntri += (unsigned)t1 + (unsigned)t2;
                 } else {
@@ -529,6 +574,50 @@ __global__ void k_pack_ss(const int* __restrict__ S, int2* __restrict__ ss, int6
         ss[e] = make_int2(S[e], TRUSS_STAMP_NONE);
 }
 
+// Dynamic shared memory of the block kernel's window instance for this graph
+// (K, C, P, Hs for the longest listed N+(u), the bitmap and its word
+// counts for the widest window), or 0 when it does not fit a block.
+template <typename Off, bool COUNT>
+size_t block_win_smem(const truss_graph* g) {
+    if (g->n_sup_big <= 0 || g->sup_big_maxup <= 0 || g->sup_big_maxup > TRUSS_SUP_BLOCK_CAP) return 0;
+    const int64_t nw = (g->sup_big_maxwin + 31) >> 5;
+    const size_t bytes = sizeof(int) * (size_t)(4 * g->sup_big_maxup + 1) + 6 * (size_t)nw;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device) != cudaSuccess) return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_support_block<Off, COUNT, true>) != cudaSuccess) return 0;
+    return bytes + fa.sharedSizeBytes <= (size_t)optin ? bytes : 0;
+}
+
+// Launches the block kernel on the listed vertices: the window instance when
+// its bitmap fits, else the binary-search one.
+template <typename Off, bool COUNT>
+int launch_block(truss_graph* g, int* S, unsigned long long* tri, HubView hv, unsigned long long* work,
+                 cudaStream_t s) {
+    const Off* rowptr = (const Off*)g->rowptr;
+    const Off* eo = (const Off*)g->eo;
+    const size_t wsm = block_win_smem<Off, COUNT>(g);
+    if (wsm) {
+        const int cap = (int)g->sup_big_maxup, nwcap = (int)((g->sup_big_maxwin + 31) >> 5);
+        CU(cudaFuncSetAttribute(k_support_block<Off, COUNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)wsm));
+        const int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms * 2);
+        k_support_block<Off, COUNT, true><<<blocks, SB_THREADS, wsm, s>>>(
+            rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S, tri, hv, work, g->n, nwcap);
+    } else {
+        const int cap = TRUSS_SUP_BLOCK_CAP;
+        const size_t smem = sizeof(int) * (size_t)(4 * cap + 1);
+        CU(cudaFuncSetAttribute(k_support_block<Off, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+        const int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
+        k_support_block<Off, COUNT><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big,
+                                                                     g->n_sup_big, cap, S, tri, hv, work);
+    }
+    CU(cudaGetLastError());
+    truss_note_launch();
+    return TRUSS_OK;
+}
+
 template <typename Off>
 int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     const Off* rowptr = (const Off*)g->rowptr;
@@ -571,18 +660,8 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
         truss_note_launch();
     }
     if (g->n_sup_big > 0) {
-        const int cap = TRUSS_SUP_BLOCK_CAP;
-        const size_t smem = sizeof(int) * (size_t)(4 * cap + 1);
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[sizeof(Off) == 8]) {
-            CU(cudaFuncSetAttribute(k_support_block<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set[sizeof(Off) == 8] = true;
-        }
-        int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
-        k_support_block<Off><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap,
-                                                              S, nullptr, hv, work);
-        CU(cudaGetLastError());
-        truss_note_launch();
+        const int rc = launch_block<Off, false>(g, S, nullptr, hv, work, s);
+        if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
@@ -618,19 +697,8 @@ int count_impl(truss_graph* g, unsigned long long* d_tri, cudaStream_t s) {
         truss_note_launch();
     }
     if (g->n_sup_big > 0) {
-        const int cap = TRUSS_SUP_BLOCK_CAP;
-        const size_t smem = sizeof(int) * (size_t)(3 * cap + 1);
-        static bool attr_set[2] = {false, false};
-        if (!attr_set[sizeof(Off) == 8]) {
-            CU(cudaFuncSetAttribute(k_support_block<Off, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-            attr_set[sizeof(Off) == 8] = true;
-        }
-        int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms);
-        k_support_block<Off, true><<<blocks, SB_THREADS, smem, s>>>(rowptr, eo, g->col, g->eid, g->sup_big,
-                                                                   g->n_sup_big, cap, nullptr, d_tri);
-        CU(cudaGetLastError());
-        truss_note_launch();
+        const int rc = launch_block<Off, true>(g, nullptr, d_tri, HubView{nullptr, nullptr, 0, 1}, nullptr, s);
+        if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);

@@ -98,6 +98,46 @@ def test_edge_list_and_support(pkt, name, g, relabel, off64):
         assert np.array_equal(eu[ids], np.minimum(a, b)) and np.array_equal(ev[ids], np.maximum(a, b))
 
 
+def _dense_core_graph(n, core, p, filler, seed):
+    """A dense random core (``core`` vertices at random labels, pairs joined
+    with probability ``p``) inside ``n`` vertices with ``filler`` random
+    edges: core vertices get N+(u) longer than a warp's 256 entries."""
+    rng = np.random.default_rng(seed)
+    c = rng.choice(n, core, replace=False).astype(np.int32)
+    iu, ju = np.triu_indices(core, 1)
+    keep = rng.random(iu.size) < p
+    src = np.concatenate([c[iu[keep]], rng.integers(0, n, filler, dtype=np.int32)])
+    dst = np.concatenate([c[ju[keep]], rng.integers(0, n, filler, dtype=np.int32)])
+    return src, dst
+
+
+@pytest.fixture(scope="module")
+def dense_core():
+    n = 1 << 21
+    src, dst = _dense_core_graph(n, 900, 0.6, 1 << 20, seed=77)
+    eu, ev = oracle.canonical(n, src, dst)
+    return n, src, dst, eu, ev, oracle.support(n, eu, ev), oracle.truss(n, eu, ev)
+
+
+@pytest.mark.parametrize("relabel,off64", [(True, False), (False, False), (True, True)])
+def test_support_block_kernel_instances(pkt, dense_core, relabel, off64):
+    """Vertices with N+(u) longer than 256 entries go to the block-per-vertex
+    support kernel: in degree order their label windows are short and N+(u)
+    is probed in a shared-memory bitmap over the window; without relabelling
+    the core sits at low labels of 2^21 (windows too wide for shared memory)
+    and the kernel searches the staged N+(u).  Support and the triangle count
+    against the oracle in both, and the support again once the peeling
+    workspace (hub bitmaps, side switch) exists."""
+    n, src, dst, eu, ev, S, T = dense_core
+    G = pkt.build_csr(dev(src), dev(dst), n, **_flags(relabel, off64))
+    assert int(np.bincount(np.concatenate([eu, ev]), minlength=n).max()) > 500
+    assert np.array_equal(host(G.support()), S)
+    assert G.triangle_count() == int(S.sum()) // 3
+    tau = host(G.decompose())
+    assert np.array_equal(host(G.support()), S)
+    assert np.array_equal(tau, T)
+
+
 # ------------------------------------------------------------ decomposition
 
 # the persistent kernel in both register budgets (the automatic choice picks
