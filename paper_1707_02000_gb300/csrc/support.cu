@@ -574,6 +574,32 @@ __global__ void k_pack_ss(const int* __restrict__ S, int2* __restrict__ ss, int6
         ss[e] = make_int2(S[e], TRUSS_STAMP_NONE);
 }
 
+// Blocks for a grid-stride kernel: no more than fit the GPU at once.  A
+// block beyond those would start only when a resident block had finished
+// its whole share, and run its own share on an emptier SM (R-MAT scale 21:
+// the 256-entry warp kernel launched 8 blocks an SM where 6 fit, and its
+// warps were active 54 % of the time against 75 % possible).
+template <typename K>
+int resident_blocks(K kern, int threads, size_t smem, int sms, int64_t want) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)per * sms));
+}
+
+// The warp-per-vertex kernel over all vertices (those beyond CAP are left
+// to the block kernels).
+template <typename Off, int CAP, bool COUNT, bool HUB>
+int launch_warp(truss_graph* g, int* S, unsigned long long* tri, HubView hv, unsigned long long* work,
+                cudaStream_t s) {
+    const int blocks = resident_blocks(k_support_warp<Off, CAP, COUNT, HUB>, SW_WARPS * 32, 0, g->sms,
+                                       ((int64_t)g->n + SW_WARPS - 1) / SW_WARPS);
+    k_support_warp<Off, CAP, COUNT, HUB><<<blocks, SW_WARPS * 32, 0, s>>>(
+        (const Off*)g->rowptr, (const Off*)g->eo, g->col, g->eid, g->n, S, tri, hv, work);
+    CU(cudaGetLastError());
+    truss_note_launch();
+    return TRUSS_OK;
+}
+
 // Dynamic shared memory of the block kernel's window instance for this graph
 // (K, C, P, Hs for the longest listed N+(u), the bitmap and its word
 // counts for the widest window), or 0 when it does not fit a block.
@@ -601,7 +627,8 @@ int launch_block(truss_graph* g, int* S, unsigned long long* tri, HubView hv, un
         const int cap = (int)g->sup_big_maxup, nwcap = (int)((g->sup_big_maxwin + 31) >> 5);
         CU(cudaFuncSetAttribute(k_support_block<Off, COUNT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)wsm));
-        const int blocks = (int)std::min<int64_t>(g->n_sup_big, (int64_t)g->sms * 2);
+        const int blocks = resident_blocks(k_support_block<Off, COUNT, true>, SB_THREADS, wsm, g->sms,
+                                           (int64_t)g->n_sup_big);
         k_support_block<Off, COUNT, true><<<blocks, SB_THREADS, wsm, s>>>(
             rowptr, eo, g->col, g->eid, g->sup_big, g->n_sup_big, cap, S, tri, hv, work, g->n, nwcap);
     } else {
@@ -642,22 +669,17 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
         // one warp-per-vertex instance: the 128-entry one when no N+(u) is
         // longer (8 blocks an SM), else the 256-entry one (6 blocks an SM);
         // two instances run one after the other cost more than either
-        int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
         const bool hub = hv.hub_of != nullptr;
+        int rc;
         if (g->max_updeg <= SW_SPLIT && hub)
-            k_support_warp<Off, SW_SPLIT, false, true>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
+            rc = launch_warp<Off, SW_SPLIT, false, true>(g, S, nullptr, hv, work, s);
         else if (g->max_updeg <= SW_SPLIT)
-            k_support_warp<Off, SW_SPLIT>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
+            rc = launch_warp<Off, SW_SPLIT, false, false>(g, S, nullptr, hv, work, s);
         else if (hub)
-            k_support_warp<Off, TRUSS_SUP_WARP_CAP, false, true>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
+            rc = launch_warp<Off, TRUSS_SUP_WARP_CAP, false, true>(g, S, nullptr, hv, work, s);
         else
-            k_support_warp<Off, TRUSS_SUP_WARP_CAP>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, S, nullptr, hv, work);
-        CU(cudaGetLastError());
-        truss_note_launch();
+            rc = launch_warp<Off, TRUSS_SUP_WARP_CAP, false, false>(g, S, nullptr, hv, work, s);
+        if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_big > 0) {
         const int rc = launch_block<Off, false>(g, S, nullptr, hv, work, s);
@@ -686,15 +708,11 @@ int count_impl(truss_graph* g, unsigned long long* d_tri, cudaStream_t s) {
     const Off* eo = (const Off*)g->eo;
     CU(cudaMemsetAsync(d_tri, 0, sizeof(unsigned long long), s));
     if (g->n > 0 && g->m > 0) {
-        int blocks = grid_for((int64_t)g->n, SW_WARPS, (int64_t)g->sms * 8);
-        if (g->max_updeg <= SW_SPLIT)
-            k_support_warp<Off, SW_SPLIT, true>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, nullptr, d_tri);
-        else
-            k_support_warp<Off, TRUSS_SUP_WARP_CAP, true>
-                <<<blocks, SW_WARPS * 32, 0, s>>>(rowptr, eo, g->col, g->eid, g->n, nullptr, d_tri);
-        CU(cudaGetLastError());
-        truss_note_launch();
+        const HubView none{nullptr, nullptr, 0, 1};
+        const int rc = g->max_updeg <= SW_SPLIT
+                           ? launch_warp<Off, SW_SPLIT, true, false>(g, nullptr, d_tri, none, nullptr, s)
+                           : launch_warp<Off, TRUSS_SUP_WARP_CAP, true, false>(g, nullptr, d_tri, none, nullptr, s);
+        if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_big > 0) {
         const int rc = launch_block<Off, true>(g, nullptr, d_tri, HubView{nullptr, nullptr, 0, 1}, nullptr, s);
