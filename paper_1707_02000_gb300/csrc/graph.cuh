@@ -45,6 +45,7 @@
 //   wrows, wdmin, wlhub   working copies of rows / dmin / lhub, rewritten
 //                     for the live edges by each compaction
 //   vstart, vend Off[n]  current row bounds of every vertex in wcol
+//   clive uint32[m/32]  live bit per edge at a compaction
 //   cbits, ctoff, cbsum  live bits per slot, per-tile and per-block offsets
 #pragma once
 #include "common.cuh"
@@ -111,6 +112,7 @@ struct truss_graph {
     int32_t *wdmin = nullptr, *wlhub = nullptr;
     void *vstart = nullptr, *vend = nullptr;
     uint32_t* cbits = nullptr;
+    uint32_t* clive = nullptr;  // one bit per edge: unprocessed at the compaction
     int32_t* ctoff = nullptr;
     long long* cbsum = nullptr;
     int cmp_ready = 0;  // compaction workspace allocated

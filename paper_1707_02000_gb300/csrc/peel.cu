@@ -1049,7 +1049,10 @@ __global__ void __launch_bounds__(PT, MINB)
 // its longer live row (searched) and the walk length dmin, which also sets
 // its light / heavy class.  So ProcessSubLevel walks min(live d(u), live
 // d(v)) entries instead of min(d(u), d(v)), and searches shorter rows.
-// Four launches over the same grid:
+// Four or five launches, A-D over the same grid:
+//   L  (graphs of 2^25 edges or more) one bit per edge: unprocessed (a
+//      sequential pass over the pairs, so the per-slot test below reads
+//      L2-resident bits, not a random pair);
 //   A  per tile of CT slots: the live bits, and the tile's offset within its
 //      block's contiguous range of tiles; per block, its live total;
 //   B  one block: exclusive prefix of the block totals;
@@ -1084,6 +1087,7 @@ struct Compactor {
     Off* rows;           // working records
     int32_t* dmin;
     int32_t* lhub;
+    const uint32_t* live;  // one bit per edge: unprocessed (k_cmp_live); nullptr: read the pairs
     uint32_t* bits;      // one bit per source slot: its edge is live
     int32_t* toff;       // per tile: live slots before it within its block's range
     long long* bsum;     // per block: live total [0, B), then its offset [B, 2B)
@@ -1095,6 +1099,20 @@ struct Compactor {
 __host__ __device__ __forceinline__ int64_t tile_lo(int64_t nt, int64_t b, int64_t B) { return nt * b / B; }
 // the block whose range holds tile t
 __device__ __forceinline__ int64_t tile_owner(int64_t nt, int64_t t, int64_t B) { return ((t + 1) * B - 1) / nt; }
+
+// live[e / 32] bit e % 32: edge e is unprocessed (stamp >= g).  One
+// sequential pass over the (S, stamp) pairs; the bits (m / 8 bytes: 33 MB
+// for R-MAT scale 24) stay in L2 for the count below, which would otherwise
+// gather a random pair -- one 32-byte sector -- for every row slot.
+__global__ void k_cmp_live(const int2* __restrict__ ss, int64_t m, int32_t g, uint32_t* __restrict__ live) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; base < m; base += stride) {
+        const int64_t e = base + lane;
+        const unsigned w = __ballot_sync(FULL_MASK, e < m && __ldg(ss + e).y >= g);
+        if (lane == 0) live[base >> 5] = w;
+    }
+}
 
 template <typename Off>
 __global__ void __launch_bounds__(PT) k_cmp_count(Compactor<Off> C) {
@@ -1110,12 +1128,14 @@ __global__ void __launch_bounds__(PT) k_cmp_count(Compactor<Off> C) {
             const int64_t s = (t + k) * CT + threadIdx.x;
             e[k] = (t + k < t1 && s < C.nslots) ? __ldg(C.eid + s) : -1;
         }
-        int st[CUN];
+        bool lv[CUN];
 #pragma unroll
-        for (int k = 0; k < CUN; k++) st[k] = e[k] >= 0 ? __ldg(&C.ss[e[k]].y) : -1;
+        for (int k = 0; k < CUN; k++)
+            lv[k] = e[k] >= 0 && (C.live ? ((__ldg(C.live + (e[k] >> 5)) >> (e[k] & 31)) & 1u)
+                                         : __ldg(&C.ss[e[k]].y) >= C.g);
 #pragma unroll
         for (int k = 0; k < CUN; k++) {
-            const unsigned b = __ballot_sync(FULL_MASK, e[k] >= 0 && st[k] >= C.g);
+            const unsigned b = __ballot_sync(FULL_MASK, lv[k]);
             if (t + k < t1) {
                 if (lane == 0) {
                     C.bits[(t + k) * CTW + warp] = b;
@@ -1501,12 +1521,14 @@ void truss_release_compaction(truss_graph* g) {
     cudaFree(g->vstart);
     cudaFree(g->vend);
     cudaFree(g->cbits);
+    cudaFree(g->clive);
     cudaFree(g->ctoff);
     cudaFree(g->cbsum);
     g->wcol = g->weid = g->tcol = g->teid = nullptr;
     g->wrows = g->vstart = g->vend = nullptr;
     g->wdmin = g->wlhub = nullptr;
     g->cbits = nullptr;
+    g->clive = nullptr;
     g->ctoff = nullptr;
     g->cbsum = nullptr;
     g->cmp_ready = 0;
@@ -1537,6 +1559,7 @@ int ensure_compaction(truss_graph* g, cudaStream_t s) {
     get(&g->vstart, osz * ((size_t)g->n + 1));
     get(&g->vend, osz * ((size_t)g->n + 1));
     get((void**)&g->cbits, sizeof(uint32_t) * CTW * ntile);
+    get((void**)&g->clive, sizeof(uint32_t) * (m / 32 + 1));
     get((void**)&g->ctoff, sizeof(int32_t) * ntile);
     get((void**)&g->cbsum, sizeof(long long) * 2 * CMP_MAX_BLOCKS);
     if (!ok) {
@@ -1598,6 +1621,11 @@ int run_compaction(truss_graph* g, CmpRun& c, int32_t gsub, int64_t processed, c
     C.rows = (Off*)g->wrows;
     C.dmin = g->wdmin;
     C.lhub = g->wlhub;
+    // graphs whose pairs outgrow L2 test the slots against live bits
+    // (R-MAT scale 24 peel 843 -> 832 ms); smaller ones read the pairs,
+    // which stay in L2 (Chung-Lu 2^20: the extra pass cost 0.15 ms)
+    const bool bits = g->m >= CMP_BIG_HELD;
+    C.live = bits ? g->clive : nullptr;
     C.bits = g->cbits;
     C.toff = g->ctoff;
     C.bsum = g->cbsum;
@@ -1605,12 +1633,13 @@ int run_compaction(truss_graph* g, CmpRun& c, int32_t gsub, int64_t processed, c
     C.hub_min = CMP_HUB_MIN_LIVE;
     if ((size_t)C.live_slots > cmp_slots(g)) return TRUSS_EINVAL;  // beyond the target's capacity
     const int B = cmp_blocks(g);
+    if (bits) k_cmp_live<<<grid_for(g->m, PT, (int64_t)g->sms * 8), PT, 0, s>>>(g->ss, g->m, gsub, g->clive);
     k_cmp_count<Off><<<B, PT, 0, s>>>(C);
     k_cmp_blocks<<<1, PT, 0, s>>>(g->cbsum, B);
     k_cmp_scatter<Off><<<B, PT, 0, s>>>(C);
     if (k > 0) k_cmp_records<Off><<<grid_for(k, 256), 256, 0, s>>>(C, list, k);
     CU(cudaGetLastError());
-    truss_note_launch(k > 0 ? 4 : 3);
+    truss_note_launch((k > 0 ? 4 : 3) + (bits ? 1 : 0));
     c.count++;
     c.slots += C.nslots;
     c.buf = dst;
@@ -2015,7 +2044,7 @@ inline int persistent_minb(const truss_graph* g, const truss_opts& o, int32_t sm
 
 // The persistent loop: one cooperative launch, or, with compaction on, one
 // launch per stretch between compactions -- each launch stops before the
-// Scan of the level whose rows are due, the host compacts them (four
+// Scan of the level whose rows are due, the host compacts them (four or five
 // launches) and resumes the loop from the state the launch left.  Each stop
 // reads that state back (one synchronisation per compaction).
 template <typename Off, int MINB>

@@ -122,6 +122,43 @@ def test_compaction_is_exact_and_walks_live_rows(pkt, name, g, loop, off64):
     G.free()
 
 
+@pytest.fixture(scope="module")
+def big_sparse():
+    """2^23 vertices, 3.4e7 random pairs plus 3000 dense communities of 12
+    to 47 vertices: more than 2^25 edges (so a compaction tests the row
+    slots against one live bit per edge instead of reading the support /
+    stamp pairs), most of them peeled at level 0, the communities up to
+    trussness 14."""
+    rng = np.random.default_rng(5)
+    n, k = 1 << 23, 34_000_000
+    src = [rng.integers(0, n, k, dtype=np.int32)]
+    dst = [rng.integers(0, n, k, dtype=np.int32)]
+    for _ in range(3000):
+        size = int(rng.integers(12, 48))
+        verts = rng.choice(n, size, replace=False).astype(np.int32)
+        iu, ju = np.triu_indices(size, 1)
+        keep = rng.random(iu.size) < 0.6
+        src.append(verts[iu[keep]])
+        dst.append(verts[ju[keep]])
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    eu, ev = oracle.canonical(n, src, dst)
+    assert eu.size >= 1 << 25
+    return n, src, dst, oracle.truss(n, eu, ev)
+
+
+@pytest.mark.parametrize("loop", ["plain", "persistent_occ"])
+@pytest.mark.parametrize("off64", [False, True])
+def test_compaction_of_a_graph_beyond_2_25_edges(pkt, big_sparse, loop, off64):
+    n, src, dst, want = big_sparse
+    G = pkt.build_csr(dev(src), dev(dst), n, offsets64=off64)
+    tau, st = G.decompose(loop=_loop(pkt, loop), stats=True)
+    assert np.array_equal(host(tau), want)
+    assert st["compactions"] > 0 and st["walked"] < st["dmin_sum"]
+    tau0, st0 = G.decompose(loop=_loop(pkt, loop), compact=0, stats=True)
+    assert np.array_equal(host(tau0), want) and st0["compactions"] == 0
+    G.free()
+
+
 @pytest.mark.parametrize("loop", LOOPS)
 def test_repeated_runs_after_compaction(pkt, loop):
     """Compaction writes only its own buffers: later runs on the same graph,
