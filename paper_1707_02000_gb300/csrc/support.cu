@@ -45,8 +45,26 @@ constexpr int SUP_SWITCH_MIN_GAIN = 10;
 
 // S accumulates in a plain int32[m] array (half the footprint of the
 // {S, stamp} pairs, so more of the random per-triangle atomics hit L2); the
-// pairs are written from it once at the end.
-__device__ __forceinline__ void add_support(int* S, int32_t e, int v) { atomicAdd(S + e, v); }
+// pairs are written from it once at the end.  When that array takes more
+// than half of L2 (beside the rows it would not stay there) but 16-bit
+// counters would take at most three quarters, and no support can exceed
+// 65535 (every degree at most 65536), two 16-bit counters share each word:
+// the geometric 2^21 graph's 134 MB become 67 MB (support 2.60 -> 2.56
+// ms; graphs whose int32 array already fits, or whose 16-bit one still
+// does not, ran 2-3 % slower with the packed adds, so they keep int32).  An add to the
+// upper half cannot carry out of the word, and one to the lower half
+// cannot carry into the upper, since neither count passes 65535.
+struct Acc {
+    int* S;
+    int s16;
+};
+
+__device__ __forceinline__ void add_support(const Acc& a, int32_t e, int v) {
+    if (a.s16)
+        atomicAdd(reinterpret_cast<unsigned*>(a.S) + (e >> 1), (unsigned)v << ((e & 1) << 4));
+    else
+        atomicAdd(a.S + e, v);
+}
 
 // Largest index p in [0, d) with P[p] <= idx (P ascending, P[0] = 0).
 __device__ __forceinline__ int seg_of(const int* P, int d, int idx) {
@@ -133,7 +151,7 @@ __device__ __forceinline__ int64_t hub_rank(const HubView& hv, int32_t h, int32_
 template <typename Off, int CAP, bool COUNT = false, bool HUB = false>
 __global__ void __launch_bounds__(SW_WARPS * 32)
     k_support_warp(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
-                   const int32_t* __restrict__ eid, int32_t n, int* __restrict__ S,
+                   const int32_t* __restrict__ eid, int32_t n, Acc S,
                    unsigned long long* __restrict__ tri = nullptr, HubView hv = HubView{nullptr, nullptr, 0, 1},
                    unsigned long long* work = nullptr) {
     __shared__ int sK[SW_WARPS][CAP];
@@ -317,7 +335,7 @@ template <typename Off, bool COUNT = false, bool WIN = false>
 __global__ void __launch_bounds__(SB_THREADS, WIN ? 2 : 1)
     k_support_block(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                     const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts, int cap,
-                    int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr,
+                    Acc S, unsigned long long* __restrict__ tri = nullptr,
                     HubView hv = HubView{nullptr, nullptr, 0, 1}, unsigned long long* work = nullptr,
                     int32_t n = 0, int nwcap = 0) {
     extern __shared__ int smem[];
@@ -507,7 +525,7 @@ template <typename Off, bool COUNT = false>
 __global__ void __launch_bounds__(SB_THREADS)
     k_support_global(const Off* __restrict__ rowptr, const Off* __restrict__ eo, const int32_t* __restrict__ col,
                      const int32_t* __restrict__ eid, const int32_t* __restrict__ verts, int32_t nverts,
-                     int* __restrict__ S, unsigned long long* __restrict__ tri = nullptr,
+                     Acc S, unsigned long long* __restrict__ tri = nullptr,
                      unsigned long long* work = nullptr) {
     unsigned long long ntri = 0, wv = 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -569,9 +587,10 @@ __global__ void k_switch_gain(const Off* __restrict__ rowptr, const Off* __restr
     if (lane == 0 && s) atomicAdd(gain, s);
 }
 
-__global__ void k_pack_ss(const int* __restrict__ S, int2* __restrict__ ss, int64_t m) {
+__global__ void k_pack_ss(Acc S, int2* __restrict__ ss, int64_t m) {
+    const unsigned short* S16 = reinterpret_cast<const unsigned short*>(S.S);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        ss[e] = make_int2(S[e], TRUSS_STAMP_NONE);
+        ss[e] = make_int2(S.s16 ? (int)S16[e] : S.S[e], TRUSS_STAMP_NONE);
 }
 
 // Blocks for a grid-stride kernel: no more than fit the GPU at once.  A
@@ -589,7 +608,7 @@ int resident_blocks(K kern, int threads, size_t smem, int sms, int64_t want) {
 // The warp-per-vertex kernel over all vertices (those beyond CAP are left
 // to the block kernels).
 template <typename Off, int CAP, bool COUNT, bool HUB>
-int launch_warp(truss_graph* g, int* S, unsigned long long* tri, HubView hv, unsigned long long* work,
+int launch_warp(truss_graph* g, Acc S, unsigned long long* tri, HubView hv, unsigned long long* work,
                 cudaStream_t s) {
     const int blocks = resident_blocks(k_support_warp<Off, CAP, COUNT, HUB>, SW_WARPS * 32, 0, g->sms,
                                        ((int64_t)g->n + SW_WARPS - 1) / SW_WARPS);
@@ -618,7 +637,7 @@ size_t block_win_smem(const truss_graph* g) {
 // Launches the block kernel on the listed vertices: the window instance when
 // its bitmap fits, else the binary-search one.
 template <typename Off, bool COUNT>
-int launch_block(truss_graph* g, int* S, unsigned long long* tri, HubView hv, unsigned long long* work,
+int launch_block(truss_graph* g, Acc S, unsigned long long* tri, HubView hv, unsigned long long* work,
                  cudaStream_t s) {
     const Off* rowptr = (const Off*)g->rowptr;
     const Off* eo = (const Off*)g->eo;
@@ -651,8 +670,12 @@ int support_impl(truss_graph* g, int2* ss, cudaStream_t s) {
     const Off* eo = (const Off*)g->eo;
     // accumulator: the first light-frontier buffer (int32[m], idle until the
     // peel starts)
-    int* S = g->fq[0][0];
-    CU(cudaMemsetAsync(S, 0, sizeof(int) * (size_t)(g->m > 0 ? g->m : 1), s));
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device) != cudaSuccess) l2 = 0;
+    const bool s16 = g->max_deg <= 65536 && 4 * g->m > (int64_t)l2 / 2 && 2 * g->m <= (int64_t)l2 * 3 / 4;
+    const Acc S{g->fq[0][0], s16 ? 1 : 0};
+    const size_t words = S.s16 ? ((size_t)g->m + 1) / 2 : (size_t)g->m;
+    CU(cudaMemsetAsync(S.S, 0, sizeof(int) * (words > 0 ? words : 1), s));
     // the hub bitmaps, when the peeling workspace has built them
     HubView hv{nullptr, nullptr, 0, 1};
     if (g->sup_switch && g->n_hub > 0 && g->hub_of && g->hub_bits)
@@ -709,19 +732,21 @@ int count_impl(truss_graph* g, unsigned long long* d_tri, cudaStream_t s) {
     CU(cudaMemsetAsync(d_tri, 0, sizeof(unsigned long long), s));
     if (g->n > 0 && g->m > 0) {
         const HubView none{nullptr, nullptr, 0, 1};
+        const Acc no{nullptr, 0};
         const int rc = g->max_updeg <= SW_SPLIT
-                           ? launch_warp<Off, SW_SPLIT, true, false>(g, nullptr, d_tri, none, nullptr, s)
-                           : launch_warp<Off, TRUSS_SUP_WARP_CAP, true, false>(g, nullptr, d_tri, none, nullptr, s);
+                           ? launch_warp<Off, SW_SPLIT, true, false>(g, no, d_tri, none, nullptr, s)
+                           : launch_warp<Off, TRUSS_SUP_WARP_CAP, true, false>(g, no, d_tri, none, nullptr, s);
         if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_big > 0) {
-        const int rc = launch_block<Off, true>(g, nullptr, d_tri, HubView{nullptr, nullptr, 0, 1}, nullptr, s);
+        const int rc =
+            launch_block<Off, true>(g, Acc{nullptr, 0}, d_tri, HubView{nullptr, nullptr, 0, 1}, nullptr, s);
         if (rc != TRUSS_OK) return rc;
     }
     if (g->n_sup_huge > 0) {
         int blocks = (int)std::min<int64_t>(g->n_sup_huge, (int64_t)g->sms * 2);
         k_support_global<Off, true><<<blocks, SB_THREADS, 0, s>>>(rowptr, eo, g->col, g->eid, g->sup_huge,
-                                                                  g->n_sup_huge, nullptr, d_tri);
+                                                                  g->n_sup_huge, Acc{nullptr, 0}, d_tri);
         CU(cudaGetLastError());
         truss_note_launch();
     }

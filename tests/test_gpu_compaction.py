@@ -128,7 +128,9 @@ def big_sparse():
     to 47 vertices: more than 2^25 edges (so a compaction tests the row
     slots against one live bit per edge instead of reading the support /
     stamp pairs), most of them peeled at level 0, the communities up to
-    trussness 14."""
+    trussness 14.  Its int32 support counters (139 MB) would take more than
+    half of L2 and 16-bit ones fit, so the support packs two counters a
+    word."""
     rng = np.random.default_rng(5)
     n, k = 1 << 23, 34_000_000
     src = [rng.integers(0, n, k, dtype=np.int32)]
@@ -143,14 +145,15 @@ def big_sparse():
     src, dst = np.concatenate(src), np.concatenate(dst)
     eu, ev = oracle.canonical(n, src, dst)
     assert eu.size >= 1 << 25
-    return n, src, dst, oracle.truss(n, eu, ev)
+    return n, src, dst, oracle.truss(n, eu, ev), oracle.support(n, eu, ev)
 
 
 @pytest.mark.parametrize("loop", ["plain", "persistent_occ"])
 @pytest.mark.parametrize("off64", [False, True])
 def test_compaction_of_a_graph_beyond_2_25_edges(pkt, big_sparse, loop, off64):
-    n, src, dst, want = big_sparse
+    n, src, dst, want, S = big_sparse
     G = pkt.build_csr(dev(src), dev(dst), n, offsets64=off64)
+    assert np.array_equal(host(G.support()), S)
     tau, st = G.decompose(loop=_loop(pkt, loop), stats=True)
     assert np.array_equal(host(tau), want)
     assert st["compactions"] > 0 and st["walked"] < st["dmin_sum"]
