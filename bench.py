@@ -59,6 +59,9 @@ WORKLOAD_DESC = {
 # the five workloads in the order of the method's evaluation configs
 CONFIG_WORKLOADS = ("rmat10_ef8", "chunglu_n2^20_d20", "rgg2d_n2^21_d32", "rmat24_ef16", "chunglu_batch4096")
 OFFSETS64 = {"rmat24_ef16"}
+# mesh-like workloads also timed in the reverse Cuthill-McKee vertex order
+# (TRUSS_LOCALITY_ORDER), a contrast beside the degree order they run in
+LOCALITY_CONTRAST = {"rgg2d_n2^21_d32"}
 # bounded CPU sample of the headline's generator for the oracle timings
 CPU_SAMPLE = dict(scale=15, edge_factor=16, seed=4)
 CPU_SAMPLE_DESC = ("oracle (serial Algorithm 1 peel, 1 core, support included) on R-MAT scale 15, edge "
@@ -551,6 +554,15 @@ def run_gpu(args):
             configs[name] = config_entry(name, c.n, Gc.m, results)
             configs[name]["contrast"] = contrast_forms(Gc, oc, ks)
             Gc.free()
+            if name in LOCALITY_CONTRAST:
+                Gl = pkt.build_csr(torch.from_numpy(c.src).cuda(), torch.from_numpy(c.dst).cuda(), c.n,
+                                   locality_order=True)
+                per, stl = timed(Gl, oc, *forms["learned"], ks, kw, params)
+                fr = form_record(per, stl)
+                configs[name]["contrast"]["locality_order"] = {
+                    "ms_per_step": fr["ms_per_step"], "support_ms": fr["ms_support"], "peel_ms": fr["ms_peel"],
+                    "wedges_up": stl[-1]["wedges_up"], "form": "persistent + learned, reverse Cuthill-McKee labels"}
+                Gl.free()
             del oc, c
     if configs:
         for i, name in enumerate(CONFIG_WORKLOADS):

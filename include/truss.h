@@ -75,6 +75,22 @@ typedef struct truss_graph truss_graph;
                                  neighbours after it.  Costs one host round
                                  trip per peel round at build time.  Takes
                                  precedence over TRUSS_DEGREE_ORDER.         */
+#define TRUSS_LOCALITY_ORDER 8u /* relabel vertices in a reverse Cuthill-McKee
+                                 order: a breadth-first search from the
+                                 vertex of highest degree (lowest label among
+                                 ties) ranks each new level by (rank of its
+                                 first-ranked neighbour in the level before,
+                                 label); the ranks are then reversed, and
+                                 vertices the search does not reach follow
+                                 in label order.  Close vertices get close
+                                 labels, so rows and the edges of a
+                                 triangle lie near each other in memory: for
+                                 mesh-like graphs (the paper orders vertices
+                                 for the same reason, §IV-B).  The support's
+                                 orientation then follows this order, not
+                                 the degree.  One host round trip per
+                                 search level at build time.  Takes
+                                 precedence over the other two orders.      */
 
 /*
  * truss_build_csr -- build the device graph of §III / Fig. 2 from a raw edge
@@ -90,7 +106,8 @@ typedef struct truss_graph truss_graph;
  *                  free them once the call has synchronised.
  *   n_in         : number of pairs (>= 0).
  *   n            : number of vertices; ids must lie in [0, n).
- *   flags        : TRUSS_DEGREE_ORDER | TRUSS_OFFSETS64.
+ *   flags        : TRUSS_DEGREE_ORDER | TRUSS_CORE_ORDER | TRUSS_LOCALITY_ORDER
+ *                  | TRUSS_OFFSETS64.
  *   out          : receives the handle (NULL on failure).
  * Synchronises `stream` before returning (the edge count sizes later
  * buffers).  Returns TRUSS_EBADGRAPH for an id outside [0, n),

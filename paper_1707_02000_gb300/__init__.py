@@ -28,6 +28,7 @@ NOALLOC_MAX_VERTICES = 1 << 22
 DEGREE_ORDER = 1
 OFFSETS64 = 2
 CORE_ORDER = 4
+LOCALITY_ORDER = 8
 LOOP_PLAIN, LOOP_PERSISTENT, LOOP_PERSISTENT_LAT, LOOP_PERSISTENT_OCC, LOOP_GRAPH = 0, 1, 2, 3, 4
 VAR_AUTO, VAR_THREAD, VAR_GROUP, VAR_WARP, VAR_LEARNED = -1, 0, 1, 2, 3
 SCHED_FEATURES, SCHED_VARIANTS, SCHED_PARAMS, TUNE_CLASSES = 5, 3, 1357, 128
@@ -342,13 +343,14 @@ class Graph:
 
 
 def build_csr(src, dst, n: int, degree_order: bool = True, offsets64: bool = False, core_order: bool = False,
-              stream=None) -> Graph:
+              locality_order: bool = False, stream=None) -> Graph:
     """Device graph from CUDA int32 tensors ``src``, ``dst`` (raw pairs);
     ``core_order`` relabels in a degeneracy (k-core) order instead of by
-    degree."""
+    degree, ``locality_order`` in a reverse Cuthill-McKee order (for
+    mesh-like graphs)."""
     assert src.dtype == dst.dtype and str(src.dtype) == "torch.int32" and src.numel() == dst.numel()
     flags = ((DEGREE_ORDER if degree_order else 0) | (OFFSETS64 if offsets64 else 0)
-             | (CORE_ORDER if core_order else 0))
+             | (CORE_ORDER if core_order else 0) | (LOCALITY_ORDER if locality_order else 0))
     h = ctypes.c_void_p()
     k = src.numel()
     _check(_lib.truss_build_csr(_dptr(src) if k else None, _dptr(dst) if k else None, k, n, flags,

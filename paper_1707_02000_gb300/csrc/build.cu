@@ -360,6 +360,162 @@ static int core_steps(const Csr64& c, int32_t n, int nb, uint64_t* keys, int32_t
     return TRUSS_OK;
 }
 
+// ---------------------------------------------------- locality (RCM) order
+//
+// A reverse Cuthill-McKee order (TRUSS_LOCALITY_ORDER): a breadth-first
+// search from the vertex of highest degree (lowest label among ties) ranks
+// each new level by (rank of its first-ranked neighbour in the level
+// before, label), so vertices close in the graph get close labels; the
+// ranks are then reversed.  Vertices the search does not reach (other
+// components, isolated vertices) follow in label order.  On mesh-like
+// graphs this keeps a vertex's rows, and the edges of its triangles, near
+// each other in memory (geometric 2^21 workload: peel 24.8 -> 22.4 ms,
+// support 2.57 -> 2.84 ms as W+ grows from 4.0e8 to 5.3e8 without the
+// degree orientation).
+
+// max over v of deg(v) << nb | (mask - v): the highest degree, then the
+// lowest label
+__global__ void k_rcm_start(const int64_t* __restrict__ rowptr, int32_t n, int nb, unsigned long long* best) {
+    const uint64_t mask = (1ull << nb) - 1;
+    unsigned long long b = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t d = (uint64_t)(rowptr[v + 1] - rowptr[v]);
+        if (d) b = max(b, (unsigned long long)(d << nb | (mask - (uint64_t)v)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(FULL_MASK, b, o));
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(best, b);
+}
+
+__global__ void k_rcm_init(int32_t n, int nb, const unsigned long long* __restrict__ best, int32_t* __restrict__ rank,
+                           int32_t* __restrict__ par, int32_t* __restrict__ level) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        rank[v] = -1;
+        par[v] = INT_MAX;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *best) {
+        const uint64_t mask = (1ull << nb) - 1;
+        level[0] = (int32_t)(mask - (*best & mask));
+    }
+}
+
+__global__ void k_rcm_seed(const int32_t* __restrict__ level, int32_t* __restrict__ rank) { rank[level[0]] = 0; }
+
+// A warp per vertex u of the current level: each unranked neighbour w keeps
+// the lowest rank among its neighbours in this level (par) and is appended
+// to the next level by the first of them.
+__global__ void k_rcm_expand(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ level, int32_t nlev, const int32_t* __restrict__ rank,
+                             int32_t* __restrict__ par, int32_t* __restrict__ cand, int* ncand) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nlev; i += nwarps) {
+        const int32_t u = level[i];
+        const int32_t ru = rank[u];
+        for (int64_t j = rowptr[u] + lane; j < rowptr[u + 1]; j += 32) {
+            const int32_t w = col[j];
+            if (rank[w] < 0 && atomicMin(par + w, ru) == INT_MAX) cand[atomicAdd(ncand, 1)] = w;
+        }
+    }
+}
+
+__global__ void k_rcm_keys(const int32_t* __restrict__ cand, int32_t k, const int32_t* __restrict__ par, int nb,
+                           uint64_t* __restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = cand[i];
+        keys[i] = (uint64_t)par[w] << nb | (uint64_t)w;
+    }
+}
+
+__global__ void k_rcm_assign(const uint64_t* __restrict__ sorted, int32_t k, uint64_t mask, int32_t base,
+                             int32_t* __restrict__ rank, int32_t* __restrict__ level) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = (int32_t)(sorted[i] & mask);
+        rank[w] = base + (int32_t)i;
+        level[i] = w;
+    }
+}
+
+struct Unranked {
+    const int32_t* rank;
+    __device__ int64_t operator()(int64_t v) const { return rank[v] < 0 ? 1 : 0; }
+};
+
+// Sort keys (n - 1 - rank) << nb | v, the unreached vertices ranked after
+// the search's in label order.
+__global__ void k_rcm_keys_final(const int32_t* __restrict__ rank, const int64_t* __restrict__ before, int32_t n,
+                                 int32_t reached, int nb, uint64_t* __restrict__ keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = rank[v] >= 0 ? rank[v] : (int64_t)reached + before[v];
+        keys[v] = (uint64_t)((int64_t)n - 1 - r) << nb | (uint64_t)v;
+    }
+}
+
+// RCM ranks as sort keys (key_bits 2 nb).  One host round trip per level.
+static int locality_keys(const Csr64& c, int32_t n, int nb, uint64_t* keys, cudaStream_t s) {
+    const int B = 256;
+    const uint64_t mask = (1ull << nb) - 1;
+    int32_t *rank = nullptr, *par = nullptr, *la = nullptr, *lb = nullptr;
+    uint64_t *kk = nullptr, *kt = nullptr;
+    int64_t* before = nullptr;
+    unsigned long long* best = nullptr;
+    int* cnt = nullptr;
+    CU(talloc(&rank, n, s));
+    CU(talloc(&par, n, s));
+    CU(talloc(&la, n, s));
+    CU(talloc(&lb, n, s));
+    CU(talloc(&kk, n, s));
+    CU(talloc(&kt, n, s));
+    CU(talloc(&before, (int64_t)n + 1, s));
+    CU(talloc(&best, 1, s));
+    CU(talloc(&cnt, 1, s));
+    CU(cudaMemsetAsync(best, 0, sizeof(unsigned long long), s));
+    k_rcm_start<<<grid_for(n, B), B, 0, s>>>(c.rowptr, n, nb, best);
+    k_rcm_init<<<grid_for(n, B), B, 0, s>>>(n, nb, best, rank, par, la);
+    CU(cudaGetLastError());
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, best, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    int32_t reached = 0;
+    if (hb) {
+        k_rcm_seed<<<1, 1, 0, s>>>(la, rank);
+        CU(cudaGetLastError());
+        int32_t nlev = 1;
+        reached = 1;
+        const int eblocks = grid_for((int64_t)n * 32, B, (int64_t)152 * 16);
+        while (nlev > 0) {
+            CU(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+            k_rcm_expand<<<eblocks, B, 0, s>>>(c.rowptr, c.col, la, nlev, rank, par, lb, cnt);
+            CU(cudaGetLastError());
+            int k = 0;
+            CU(cudaMemcpyAsync(&k, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            if (k == 0) break;
+            k_rcm_keys<<<grid_for(k, B), B, 0, s>>>(lb, k, par, nb, kk);
+            CU(cudaGetLastError());
+            uint64_t* sorted = nullptr;
+            CU(prims::radix_sort_u64(kk, kt, k, 2 * nb, &sorted, s));
+            k_rcm_assign<<<grid_for(k, B), B, 0, s>>>(sorted, k, mask, reached, rank, la);
+            CU(cudaGetLastError());
+            reached += k;
+            nlev = k;
+        }
+    }
+    CU(prims::exclusive_scan<int64_t>(Unranked{rank}, n, before, before + n, s));
+    k_rcm_keys_final<<<grid_for(n, B), B, 0, s>>>(rank, before, n, reached, nb, keys);
+    CU(cudaGetLastError());
+    tfree(rank, s);
+    tfree(par, s);
+    tfree(la, s);
+    tfree(lb, s);
+    tfree(kk, s);
+    tfree(kt, s);
+    tfree(before, s);
+    tfree(best, s);
+    tfree(cnt, s);
+    return TRUSS_OK;
+}
+
 // CSR (64-bit offsets) from 2m sorted unique directed keys.
 int csr_from_keys(const uint64_t* U, int64_t len, int32_t n, int nb, Csr64& c, cudaStream_t s) {
     const int B = 256;
@@ -431,8 +587,9 @@ int build_impl(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t
     TRY(csr_from_keys(U, two_m, n, nb, c0, s));
     Csr64 c1;
     uint64_t* U1 = U;
-    const bool core_order = (flags & TRUSS_CORE_ORDER) && n > 1;
-    const bool relabel = ((flags & TRUSS_DEGREE_ORDER) || core_order) && n > 1;
+    const bool locality_order = (flags & TRUSS_LOCALITY_ORDER) && n > 1;
+    const bool core_order = (flags & TRUSS_CORE_ORDER) && !locality_order && n > 1;
+    const bool relabel = ((flags & TRUSS_DEGREE_ORDER) || core_order || locality_order) && n > 1;
     int32_t* newid = nullptr;
     if (relabel) {
         // 4: rank by (degree, label); a degree is below 2^nb
@@ -440,7 +597,9 @@ int build_impl(const int32_t* d_src, const int32_t* d_dst, int64_t n_in, int32_t
         CU(talloc(&dk, n, s));
         CU(talloc(&dtmp, n, s));
         int key_bits = 2 * nb;
-        if (core_order) {
+        if (locality_order) {
+            TRY(locality_keys(c0, n, nb, dk, s));
+        } else if (core_order) {
             int32_t rounds = 0;
             TRY(core_steps(c0, n, nb, dk, &rounds, s));
             int rb = 1;

@@ -32,12 +32,12 @@ def pkt():
     return pkt
 
 
-def _run(pkt, g, loop):
+def _run(pkt, g, loop, locality=False):
     import torch
 
     src = torch.from_numpy(g.src).cuda()
     dst = torch.from_numpy(g.dst).cuda()
-    G = pkt.build_csr(src, dst, g.n)
+    G = pkt.build_csr(src, dst, g.n, locality_order=locality)
     step = torch.empty(G.m, dtype=torch.int32, device="cuda")
     tau, st = G.decompose(loop=loop, peel_step=step, stats=True)
     S = G.support()
@@ -47,10 +47,13 @@ def _run(pkt, g, loop):
     return out
 
 
-@pytest.mark.parametrize("name", ["chunglu_n2^20_d20", "rgg2d_n2^21_d32"])
-def test_full_size_certified(pkt, name):
+@pytest.mark.parametrize("name,locality", [("chunglu_n2^20_d20", False), ("rgg2d_n2^21_d32", False),
+                                           ("rgg2d_n2^21_d32", True)])
+def test_full_size_certified(pkt, name, locality):
+    """Certified over every edge in the timed launch configuration, and for
+    the geometric workload also in the reverse Cuthill-McKee order."""
     g = gg.workload(name)
-    u, v, tau, step, S, st = _run(pkt, g, pkt.LOOP_PERSISTENT)
+    u, v, tau, step, S, st = _run(pkt, g, pkt.LOOP_PERSISTENT, locality)
     eu, ev = oracle.canonical(g.n, g.src, g.dst)
     assert np.array_equal(u, eu) and np.array_equal(v, ev)
     bad, first = oracle.certify(g.n, eu, ev, tau, step)

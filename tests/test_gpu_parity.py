@@ -433,6 +433,66 @@ def test_core_order_is_a_degeneracy_order_and_exact(pkt, loop):
         G.free()
 
 
+def _rcm_host(n, eu, ev):
+    """Reverse Cuthill-McKee labels written out on the host: breadth-first
+    search from the vertex of highest degree (lowest label among ties); each
+    new level in order of (lowest rank among its neighbours in the level
+    before, label); ranks reversed; unreached vertices first, in label
+    order.  Returns the input label of each internal label."""
+    adj = [[] for _ in range(n)]
+    for a, b in zip(eu.tolist(), ev.tolist()):
+        adj[a].append(b)
+        adj[b].append(a)
+    deg = np.array([len(r) for r in adj])
+    rank = {}
+    if deg.max(initial=0) > 0:
+        s = int(np.flatnonzero(deg == deg.max())[0])
+        rank[s] = 0
+        level = [s]
+        while level:
+            par = {}
+            for u in level:
+                for w in adj[u]:
+                    if w not in rank:
+                        par[w] = min(par.get(w, n), rank[u])
+            level = sorted(par, key=lambda w: (par[w], w))
+            for w in level:
+                rank[w] = len(rank)
+    reached = len(rank)
+    for v in range(n):
+        if v not in rank:
+            rank[v] = len(rank)
+    order = np.empty(n, np.int64)
+    for v, r in rank.items():
+        order[n - 1 - r] = v
+    return order, reached
+
+
+@pytest.mark.parametrize("loop", ["plain", "persistent"])
+def test_locality_order_is_rcm_and_exact(pkt, loop):
+    """With TRUSS_LOCALITY_ORDER the internal labels are the reverse
+    Cuthill-McKee order the host restatement gives, vertex for vertex
+    (connected and disconnected graphs, isolated vertices); the edge list,
+    the support and the trussness are the oracle's."""
+    two = gg.small_random(50, 0.3, seed=41)
+    union = gg.EdgeList(230, np.concatenate([two.src, two.src + 60, np.array([120, 121, 122], np.int32)]),
+                        np.concatenate([two.dst, two.dst + 60, np.array([121, 122, 120], np.int32)]), "union")
+    graphs = [gg.workload("rmat10_ef8"), gg.chung_lu(6000, 2.1, 12.0, 600.0, seed=21),
+              gg.rgg2d(5000, 14.0, seed=22), union]
+    for g in graphs:
+        G = pkt.build_csr(dev(g.src), dev(g.dst), g.n, locality_order=True)
+        eu, ev, want = oracle.truss_of_edges(g.n, g.src, g.dst)
+        u, v = G.edge_list()
+        assert np.array_equal(host(u), eu) and np.array_equal(host(v), ev), g.name
+        assert np.array_equal(host(G.support()), oracle.support(g.n, eu, ev)), g.name
+        assert np.array_equal(host(G.decompose(loop=_loop(pkt, loop))), want), g.name
+        rp, col, eid, eo, order = (host(x) for x in G.csr())
+        want_order, reached = _rcm_host(g.n, eu, ev)
+        assert np.array_equal(order, want_order), g.name
+        assert 0 < reached <= g.n
+        G.free()
+
+
 def _want_bps(st):
     per_level = st["dmin_sum"] // (st["max_support"] + 1)
     return 6 if per_level >= 1 << 24 or st["dmin_sum"] >= 1 << 34 else 4
