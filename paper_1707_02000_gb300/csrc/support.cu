@@ -18,11 +18,17 @@
 //    on the geometric workload than the 256-entry one at 6 blocks an SM);
 //    else the 256-entry one;
 //    the 32 lanes then walk the concatenation of all N+(v) lists as one flat
-//    range (balanced within the warp, coalesced reads of each N+(v)), and
-//    probe each w by binary search in the staged N+(u);
+//    range (balanced within the warp, coalesced reads of each N+(v); a
+//    lane's segment only moves forward, see seg_advance), and probe each w
+//    by binary search in the staged N+(u);
 //  - block per vertex for larger d+(u) (listed at build time), same scheme
-//    with the block's shared memory;
+//    with the block's shared memory, its warps taking chunks of the flat
+//    range; when the label windows above the listed vertices fit shared
+//    memory (degree order puts these vertices at the top), N+(u) is also a
+//    bitmap over its window and a probe is one word read;
 //  - global-memory fallback for d+(u) beyond the shared-memory capacity.
+// Every grid-stride launch is sized to the blocks that fit the GPU at once
+// (resident_blocks).
 // Supports of the edges {u, x}, x in N+(u), are accumulated in shared
 // counters and added once per edge; only the {v, w} edges take one global
 // atomic per triangle.
