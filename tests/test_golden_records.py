@@ -18,7 +18,7 @@ def _read(path):
         if f[0] == "hist":
             hist[int(f[1])] = int(f[2])
         else:
-            rec[f[0]] = f[1]
+            rec.update(zip(f[0::2], f[1::2]))  # "key value" pairs, one or more a line
     return rec, hist
 
 
